@@ -1,0 +1,407 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: the paper's worked
+example, closed-form noise statistics, exhaustive enumeration, special cases with a known
+answer and finite differences.  A dropped term, a wrong index, a flipped comparison or a
+transposed operand in ``oracle/hs_oracle.c`` fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def unit_norm(H):
+    return np.zeros(H), np.ones(H)
+
+
+def drift_of(path, H):
+    """Drift after each order: D_k = popcount(path & ((1 << k) - 1))."""
+    return [bin(int(path) & ((1 << k) - 1)).count("1") for k in range(1, H + 1)]
+
+
+# ----------------------------------------------------------------------------------------
+# special cases
+# ----------------------------------------------------------------------------------------
+def test_h1_returns_input(oracle_lib):
+    o = oracle_lib
+    x = synth.spectrum(1000, 11)
+    mu, sg = unit_norm(1)
+    nf = o.nf_1d(x.size, 1)
+    assert nf == x.size - 1
+    s, bh = o.simple_1d(x, 1, mu, sg)
+    assert np.array_equal(s, x[:nf].astype(np.float64)) and np.all(bh == 1)
+    g, bh, path = o.greedy_1d(x, 1, mu, sg, mitigation=False)
+    assert np.array_equal(g, x[:nf].astype(np.float64)) and np.all(path == 0)
+    g, bh, path = o.greedy_1d(x, 1, mu, sg, mitigation=True)
+    assert np.array_equal(g, np.maximum(x[:nf], x[1:nf + 1]).astype(np.float64))
+    assert np.array_equal(path, (x[1:nf + 1] > x[:nf]).astype(np.uint32))
+
+
+def test_domain(oracle_lib):
+    o = oracle_lib
+    assert o.nf_1d(131072, 32) == 4095
+    assert o.nf_1d(1 << 23, 32) == 262143
+    assert o.nf_1d(33, 32) == 1 and o.nf_1d(32, 32) == 0
+    # the greedy form's largest read, H*n + H, is the last bin for the largest n
+    N, H = 1000, 7
+    nf = o.nf_1d(N, H)
+    assert H * (nf - 1) + H <= N - 1 < H * nf + H
+
+
+def test_monotone_spectra(oracle_lib):
+    o = oracle_lib
+    N, H = 4096, 16
+    mu, sg = unit_norm(H)
+    dec = (N - np.arange(N)).astype(np.float32)          # strictly decreasing: never drift
+    s_all = o.simple_1d(dec, H, mu, sg, want_all=True)[2]
+    g_all = o.greedy_1d(dec, H, mu, sg, want_all=True)[3]
+    path = o.greedy_1d(dec, H, mu, sg)[2]
+    assert np.all(path == 0)
+    assert np.array_equal(s_all, g_all)
+    n = np.arange(s_all.shape[0])[:, None]
+    h = np.arange(1, H + 1)[None, :]
+    assert np.array_equal(s_all, N * h - n * h * (h + 1) / 2)    # sum_k (N - k n)
+    inc = np.arange(N).astype(np.float32)                  # strictly increasing: drift every order
+    g_all = o.greedy_1d(inc, H, mu, sg, want_all=True)[3]
+    path = o.greedy_1d(inc, H, mu, sg)[2]
+    assert np.all(path == (1 << H) - 1)
+    assert np.array_equal(g_all, (n + 1) * h * (h + 1) / 2)       # sum_k (k n + k)
+    path_nm = o.greedy_1d(inc, H, mu, sg, mitigation=False)[2]
+    assert np.all(path_nm == (1 << H) - 2)
+
+
+def test_snr_normalisation_and_best_h(oracle_lib):
+    """Eq. 2: SNR_h = (S_h - mu_h) / sigma_h, max over h, lowest h on ties."""
+    o = oracle_lib
+    N, H = 2048, 8
+    x = synth.small_int_spectrum(N, 5)
+    mu = np.arange(1, H + 1) * 3.5
+    sg = np.sqrt(np.arange(1, H + 1)) * 2.0
+    for fn in (lambda m, s: o.simple_1d(x, H, m, s, want_all=True),
+               lambda m, s: o.greedy_1d(x, H, m, s, want_all=True)):
+        raw = fn(np.zeros(H), np.ones(H))[-1]                 # raw partial sums S_h
+        out = fn(mu, sg)
+        snr, bh, allv = out[0], out[1], out[-1]
+        np.testing.assert_allclose(allv, (raw - mu) / sg, rtol=0, atol=1e-12)
+        first_max = np.argmax(allv, axis=1) + 1               # numpy argmax = lowest index on ties
+        assert np.array_equal(bh, first_max)
+        assert np.array_equal(snr, allv[np.arange(allv.shape[0]), bh - 1])
+    # ties: an all-zero spectrum with zero mean gives equal SNRs -> best h is 1
+    z = np.zeros(300, np.float32)
+    assert np.all(o.greedy_1d(z, 8, np.zeros(8), np.ones(8))[1] == 1)
+    assert np.all(o.simple_1d(z, 8, np.zeros(8), np.ones(8))[1] == 1)
+
+
+def test_greedy_strict_tie_keeps_drift(oracle_lib):
+    """A tie x[m+1] == x[m] keeps the drift (the comparison is strict, Algorithm 2)."""
+    o = oracle_lib
+    x = np.ones(200, np.float32)
+    assert np.all(o.greedy_1d(x, 8, *unit_norm(8))[2] == 0)
+
+
+# ----------------------------------------------------------------------------------------
+# the paper's worked example and the injected pulse train
+# ----------------------------------------------------------------------------------------
+def _sinc2(d):
+    d = np.asarray(d, np.float64)
+    out = np.ones_like(d)
+    nz = d != 0
+    out[nz] = (np.sin(np.pi * d[nz]) / (np.pi * d[nz])) ** 2
+    return out
+
+
+def test_fig2_drift(oracle_lib):
+    """Sec. 2.2 / Fig. 2: a 10.1245 Hz pulsar in 0.05 Hz bins drifts by {0,1,1,2,2} bins."""
+    o = oracle_lib
+    gold = json.load(open(os.path.join(GOLD, "fig2_drift.json")))
+    f_bins = gold["pulsar_hz"] / gold["bin_width_hz"]
+    H = len(gold["orders"])
+    N = 4096
+    j = np.arange(N)
+    x = np.zeros(N)
+    for h in gold["orders"]:
+        x += _sinc2(j - h * f_bins)        # noise-free DFT power of each harmonic
+    x = x.astype(np.float32)
+    n = gold["fundamental_bin"]
+    assert [int(np.argmax(x[h * n - 5:h * n + 6]) + h * n - 5) for h in gold["orders"]] == gold["nearest_bins"]
+    path = o.greedy_1d(x, H, *unit_norm(H))[2]
+    assert drift_of(path[n], H) == gold["drift"]
+    # the simple sum stays on the integer multiples: it collects the fundamental only
+    s = o.simple_1d(x, H, *unit_norm(H), want_all=True)[2]
+    g = o.greedy_1d(x, H, *unit_norm(H), want_all=True)[3]
+    assert g[n, -1] > s[n, -1] + 1.5
+
+
+def test_pulse_train_noise_free(oracle_lib):
+    o = oracle_lib
+    gold = json.load(open(os.path.join(GOLD, "pulse_train_1234.json")))
+    H, n = gold["H"], gold["fundamental_bin"]
+    pul = synth.Pulsar(gold["f0_bins"], gold["duty"], gold["amplitude"])
+    x = synth.inject(np.zeros(synth.CONFIG1_N, np.float32), [pul])
+    s_all = o.simple_1d(x, H, *unit_norm(H), want_all=True)[2]
+    g_all = o.greedy_1d(x, H, *unit_norm(H), want_all=True)[3]
+    path = o.greedy_1d(x, H, *unit_norm(H))[2]
+    assert drift_of(path[n], H)[:8] == gold["drift_first_8"]
+    k = np.arange(1, H + 1)
+    expect = np.cumsum(gold["amplitude"] * np.exp(-(np.pi * gold["duty"] * k) ** 2))
+    np.testing.assert_allclose(g_all[n], expect, rtol=1e-6)       # float32-stored powers
+    assert abs(g_all[n, -1] - 41.13516668) < 1e-4
+    np.testing.assert_allclose(s_all[n], np.full(H, expect[0]), rtol=1e-6)
+    assert abs(s_all[n, 0] - 7.80502323) < 1e-5
+
+
+def test_pulse_train_recovered_in_noise(oracle_lib):
+    o = oracle_lib
+    x = synth.single_pulse_spectrum()
+    H = 32
+    mu_s, sg_s = o.norm_exponential(1, 1, H)
+    mu_g, sg_g = o.norm_exponential(2, 1, H)
+    ss, _ = o.simple_1d(x, H, mu_s, sg_s)
+    gs, gh, _ = o.greedy_1d(x, H, mu_g, sg_g)
+    assert int(np.argmax(gs)) == 1234
+    assert gs[1234] > ss[1234]
+    assert gh[1234] > 1          # several harmonics add SNR (power ~ noise mean past k ~ 8)
+
+
+# ----------------------------------------------------------------------------------------
+# noise statistics (Eq. 2's mu_H, sigma_H for exponential noise)
+# ----------------------------------------------------------------------------------------
+def _moment_check(samples, mean, var, nsig=5.0):
+    m = samples.mean(axis=0)
+    v = samples.var(axis=0, ddof=1)
+    cnt = samples.shape[0]
+    se_m = np.sqrt(var / cnt)
+    c = samples - m
+    m4 = (c ** 4).mean(axis=0)
+    se_v = np.sqrt(np.maximum(m4 - v ** 2, 1e-30) / cnt)
+    assert np.all(np.abs(m - mean) < nsig * se_m), (m, mean)
+    assert np.all(np.abs(v - var) < nsig * se_v), (v, var)
+
+
+def test_exp_noise_moments(oracle_lib):
+    """Simple: S_h ~ Gamma(h, 1) (mean h, var h).  Greedy: each order adds the max of two fresh
+    Exp(1) draws (mean 3/2, var 5/4) -- fresh because order h reads bins > n past order h-1."""
+    o = oracle_lib
+    N, H = 1 << 21, 32
+    x = synth.exp_noise(N, 99)
+    h = np.arange(1, H + 1, dtype=np.float64)
+    s_all = o.simple_1d(x, H, *unit_norm(H), want_all=True)[2][2:]
+    _moment_check(s_all, h, h)
+    g_all = o.greedy_1d(x, H, *unit_norm(H), want_all=True)[3][2:]
+    _moment_check(g_all, 1.5 * h, 1.25 * h)
+    g_nm = o.greedy_1d(x, H, *unit_norm(H), mitigation=False, want_all=True)[3][2:]
+    _moment_check(g_nm, 1 + 1.5 * (h - 1), 1 + 1.25 * (h - 1))
+    # closed forms used for normalisation agree with the measured moments
+    for form, mit, samp in ((1, True, s_all), (2, True, g_all), (2, False, g_nm)):
+        mu, sg = o.norm_exponential(form, 1, H, mitigation=mit)
+        _moment_check(samp, mu, sg ** 2)
+
+
+def test_snr_standardised_on_noise(oracle_lib):
+    o = oracle_lib
+    N, H = 1 << 20, 16
+    x = synth.exp_noise(N, 7)
+    mu, sg = o.norm_exponential(2, 1, H)
+    allv = o.greedy_1d(x, H, mu, sg, want_all=True)[3][2:]
+    assert np.all(np.abs(allv.mean(axis=0)) < 0.02)
+    assert np.all(np.abs(allv.std(axis=0) - 1) < 0.02)
+
+
+# ----------------------------------------------------------------------------------------
+# exhaustive search and the optimal path
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mitigation", [True, False])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_brute_force_bounds_and_reproduces_greedy(oracle_lib, mitigation, seed):
+    o = oracle_lib
+    N, H = 96, 7
+    for x in (synth.exp_noise(N, seed), synth.small_int_spectrum(N, seed, 4)):
+        g_all = o.greedy_1d(x, H, *unit_norm(H), mitigation=mitigation, want_all=True)
+        paths, allv = g_all[2], g_all[3]
+        for n in range(o.nf_1d(N, H)):
+            best, rule_path, rule_count = o.brute_1d(x, H, n, mitigation=mitigation)
+            dp = o.dp_1d(x, H, n, mitigation=mitigation)
+            assert rule_count == 1
+            assert rule_path == paths[n]
+            np.testing.assert_allclose(best, dp, rtol=0, atol=1e-12)
+            assert np.all(allv[n] <= best + 1e-12)
+
+
+def test_path_invariants(oracle_lib):
+    """d_m(h) = h-1 between fundamentals (Sec. 2.2); the fundamental comparison adds at most 1."""
+    o = oracle_lib
+    N, H = 1 << 16, 32
+    x = synth.exp_noise(N, 3)
+    for mit in (True, False):
+        path = o.greedy_1d(x, H, *unit_norm(H), mitigation=mit)[2]
+        for k in (1, 2, 5, 17, 32):
+            mask = np.uint32((1 << k) - 1) if k < 32 else np.uint32(0xFFFFFFFF)
+            D = np.array([bin(int(v)).count("1") for v in (path & mask)])
+            assert D.max() <= (k if mit else k - 1)
+        if not mit:
+            assert np.all((path & 1) == 0)
+
+
+# ----------------------------------------------------------------------------------------
+# adjoint vs finite differences (FP64, whitening kept exact so the forward is piecewise linear)
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("form", [1, 2])
+def test_backward_matches_finite_differences(oracle_lib, form):
+    o = oracle_lib
+    N, H = 1024, 8
+    p = synth.exp_noise(N, 21)
+    w = synth.whitening(N, 22)
+    mu, sg = o.norm_exponential(form, 1, H)
+    nf = o.nf_1d(N, H)
+    g = synth.upstream_grad(nf, 23).astype(np.float64)
+
+    def fwd(wv):
+        if form == 1:
+            s, bh = o.simple_1d(p, H, mu, sg, w=wv, round_w=False)
+            return s, bh, None
+        return o.greedy_1d(p, H, mu, sg, w=wv, round_w=False)
+
+    s0, bh0, path0 = fwd(w)
+    gx = o.backward_1d(form, N, H, bh0, sg, g, path0)
+    gw = gx * p                                    # dL/dw = p * dL/dx for x = w p
+    eps = 1e-3
+    rs = np.random.default_rng(5)
+    js = rs.choice(H * nf, size=120, replace=False)
+    checked = 0
+    for j in js:
+        wp, wm = w.astype(np.float64).copy(), w.astype(np.float64).copy()
+        wp[j] += eps
+        wm[j] -= eps
+        outp, outm = fwd(wp.astype(np.float32)), fwd(wm.astype(np.float32))
+        # keep w in float32 for the oracle input: use the exact float32 perturbation size
+        dw = float(np.float32(wp[j])) - float(np.float32(wm[j]))
+        same = all(np.array_equal(a, b) for a, b in zip(outp[1:], (bh0, path0)) if b is not None) and \
+            all(np.array_equal(a, b) for a, b in zip(outm[1:], (bh0, path0)) if b is not None)
+        if not same:
+            continue
+        fd = (np.dot(g, outp[0]) - np.dot(g, outm[0])) / dw
+        assert abs(fd - gw[j]) <= 1e-7 * max(1.0, abs(gw[j])), (j, fd, gw[j])
+        checked += 1
+    assert checked > 60
+
+
+def test_backward_counts_each_chosen_bin(oracle_lib):
+    """With g = sigma_{h*}, dL/dx counts how many (n, k <= h*) chose each bin."""
+    o = oracle_lib
+    N, H = 512, 6
+    x = synth.exp_noise(N, 8)
+    mu, sg = o.norm_exponential(2, 1, H)
+    _, bh, path = o.greedy_1d(x, H, mu, sg)
+    g = sg[bh.astype(np.int64) - 1]
+    gx = o.backward_1d(2, N, H, bh, sg, g, path)
+    assert np.isclose(gx.sum(), bh.astype(np.int64).sum())
+    assert np.all(gx == np.round(gx))
+    gx_s = o.backward_1d(1, N, H, bh, sg, g)
+    n = np.arange(bh.size)
+    assert gx_s[0] == bh.astype(np.int64)[0]              # fundamental 0 puts all its orders on bin 0
+    assert gx_s[n[1:]].min() >= 1                          # every fundamental's own bin (k = 1)
+
+
+# ----------------------------------------------------------------------------------------
+# 2D
+# ----------------------------------------------------------------------------------------
+def test_2d_domain(oracle_lib):
+    assert oracle_lib.domain_2d(1 << 21, 201, 100, 8) == (1, 262142, -11, 11)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_2d_brute_force(oracle_lib, seed):
+    o = oracle_lib
+    H, z0 = 3, 6
+    pl = synth.plane(40, 2 * z0 + 1, z0, seed)
+    pl_int = np.floor(pl).astype(np.float32)             # dense ties exercise the raster rule
+    for P in (pl, pl_int):
+        dom = o.domain_2d(P.shape[1], P.shape[0], z0, H)
+        snr, bh, path, allv = o.greedy_2d(P, z0, H, *unit_norm(H), want_all=True)
+        f_lo, f_hi, z_lo, z_hi = dom
+        nff = f_hi - f_lo + 1
+        for z in range(z_lo, z_hi + 1):
+            for f in range(f_lo, f_hi + 1, 3):
+                i = (z - z_lo) * nff + (f - f_lo)
+                best, rp, rc = o.brute_2d(P, z0, H, f, z)
+                assert rc == 1 and rp == path[i]
+                assert np.all(allv[i] <= best + 1e-12)
+
+
+def test_2d_noise_moments(oracle_lib):
+    """chi-square(2) noise: each 2D order adds the max of 9 fresh draws of mean 2
+    (fresh for f >= 4): mean 2 H_9 per order, variance 4 sum_{k<=9} 1/k^2 per order."""
+    o = oracle_lib
+    H, z0 = 4, 20
+    pl = synth.plane(1 << 15, 2 * z0 + 1, z0, 31)
+    dom = o.domain_2d(pl.shape[1], pl.shape[0], z0, H)
+    dom = (4, dom[1], dom[2], dom[3])
+    allv = o.greedy_2d(pl, z0, H, *unit_norm(H), dom=dom, want_all=True)[3]
+    h = np.arange(1, H + 1, dtype=np.float64)
+    H9 = sum(1.0 / k for k in range(1, 10))
+    S9 = sum(1.0 / k ** 2 for k in range(1, 10))
+    # rows of different z share no bins for f >= 4 only within a row band; moments are robust
+    _moment_check(allv, 2 * H9 * h, 4 * S9 * h, nsig=6)
+    mu, sg = o.norm_exponential(2, 2, H, mean1=2.0)
+    _moment_check(allv, mu, sg ** 2, nsig=6)
+
+
+def test_2d_noise_free_track(oracle_lib):
+    """A signal whose harmonic k sits at (k*zf, k*ff) with |fractional parts| < 1/2 is followed
+    bin by bin: the drift at order k is (round(k*ff) - k*f, round(k*zf) - k*z)."""
+    o = oracle_lib
+    H, z0, nfreq = 8, 100, 1 << 14
+    ff, zf = 1000.3, -3.4
+    f, z = 1000, -3
+    pl = np.zeros((2 * z0 + 1, nfreq), np.float32)
+    amp = [8 * math.exp(-(math.pi * 0.05 * k) ** 2) for k in range(1, H + 1)]
+    for k in range(1, H + 1):
+        pl[z0 + int(round(k * zf)), int(round(k * ff))] += amp[k - 1]
+    dom = o.domain_2d(nfreq, 2 * z0 + 1, z0, H)
+    snr, bh, path, allv = o.greedy_2d(pl, z0, H, *unit_norm(H), want_all=True)
+    i = (z - dom[2]) * (dom[1] - dom[0] + 1) + (f - dom[0])
+    np.testing.assert_allclose(allv[i], np.cumsum(np.float32(amp).astype(np.float64)), rtol=1e-12)
+    df = dz = 0
+    for k in range(1, H + 1):
+        code = (int(path[i]) >> (4 * (k - 1))) & 0xF
+        df += code % 3 - 1
+        dz += code // 3 - 1
+        assert df == int(round(k * ff)) - k * f and dz == int(round(k * zf)) - k * z
+
+
+# ----------------------------------------------------------------------------------------
+# sector footprint (compulsory input bytes)
+# ----------------------------------------------------------------------------------------
+def test_sector_footprint(oracle_lib):
+    o = oracle_lib
+    N, H = 1 << 14, 1
+    nf = o.nf_1d(N, H)
+    assert o.sectors_1d(1, 4, N, H) == -(-nf // 8)            # order 1 reads bins 0..nf-1
+    assert o.sectors_1d(1, 2, N, H) == -(-nf // 16)
+    # strictly increasing input: greedy reads h n + d, d = h-1 and h -> bins up to H n + H
+    H = 4
+    inc = np.arange(N, dtype=np.float32)
+    path = o.greedy_1d(inc, H, *unit_norm(H))[2]
+    nf = o.nf_1d(N, H)
+    reads = set()
+    for n in range(nf):
+        reads.update({n, n + 1})
+        for h in range(2, H + 1):
+            reads.update({h * n + h - 1, h * n + h})
+    assert o.sectors_1d(2, 4, N, H, path=path) == len({r // 8 for r in reads})
+    # on noise, fused simple + greedy at H = 32 touch most (not all) sectors; the greedy form
+    # alone touches a subset of the fused footprint, which contains the simple one
+    x = synth.exp_noise(1 << 20, 1)
+    path = o.greedy_1d(x, 32, *unit_norm(32))[2]
+    both = o.sectors_1d(3, 4, 1 << 20, 32, path=path)
+    g = o.sectors_1d(2, 4, 1 << 20, 32, path=path)
+    s = o.sectors_1d(1, 4, 1 << 20, 32)
+    assert max(g, s) <= both <= (1 << 20) // 8
+    assert both > 0.95 * (1 << 20) // 8
