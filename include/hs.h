@@ -1,0 +1,169 @@
+/*
+ * hs.h -- C ABI of libhs.so: the incoherent harmonic sum on one GB300 (sm_103a).
+ *
+ * Method: Adamek, Roy & Armour, "A Novel Greedy Approach To Harmonic Summing Using GPUs"
+ * (arXiv:2202.12817).  For every fundamental bin n of a power spectrum x (1D) or every
+ * fundamental (f, z) of an f-fdot plane (2D) the library forms the partial sums of the
+ * harmonic orders h = 1..H, normalises each to an SNR with the caller's mean and standard
+ * deviation of an h-term sum (Eq. 2), and reports the maximum SNR, the h that reached it and,
+ * for the greedy form, the drift path.
+ *
+ *   simple form (Eq. 3):   S_h[n] = sum_{k=1..h} x[k n]
+ *   greedy form (Eq. 5, Algorithm 2): d = 0; at order 1 (with scalloping-loss mitigation,
+ *       the default) compare x[n], x[n+1]; at order h >= 2 compare x[m], x[m+1] with
+ *       m = h n + d; if the second is strictly larger, d += 1 and it is summed, else the
+ *       first is summed.  Path bit h-1 records the increment at order h.
+ *   2D greedy: centre (h f + df, h z + dz), best of the 3x3 neighbourhood (centre first, then
+ *       raster order dz = -1..1, df = -1..1, strictly larger replaces), 4-bit code
+ *       (oz+1)*3 + (of+1) per order at bits 4(h-1)..4h-1.
+ *   SNR_h = (S_h - mu[h-1]) / sigma[h-1]; the maximum over h starts at h = 1 and is replaced
+ *       only by a strictly larger value (lowest h wins ties).
+ *
+ * Fundamental domain: 1D n in [0, N_f) with N_f = floor((N-1)/H) -- every read of both forms
+ * (largest: H n + H) lies inside the spectrum.  2D: f in [1, (n_freq-1-H)/H] and the z for which
+ * rows z0_row + h z +- h stay inside the plane for all h (see hs_plan_domain_2d).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device addresses on the plan's device; the caller owns and
+ *     allocates every device buffer.  Device pointers must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - hs_run and hs_backward never allocate and never synchronise the host.
+ *   - Errors are returned as hs_status; nothing throws or aborts across the ABI.  Errors that
+ *     only a kernel can see (HS_FLAG_CHECKED) set the plan's device error word, read and
+ *     cleared by hs_check_device_error.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_INVALID_ARG = 1,    /* a null/misaligned pointer, out-of-range size or flag */
+    HS_ERR_UNSUPPORTED = 2,    /* valid but not provided (e.g. a 2D simple form) */
+    HS_ERR_OOM = 3,            /* plan-owned device/host allocation failed (plan creation only) */
+    HS_ERR_CUDA = 4,           /* a CUDA runtime call failed; see hs_last_cuda_error */
+    HS_ERR_DEVICE_BOUNDS = 5,  /* a checked kernel saw an index outside its buffer */
+    HS_ERR_DEVICE_TIMEOUT = 6, /* a bounded device wait gave up */
+    HS_ERR_NO_DEVICE = 7       /* plan made with HS_FLAG_NO_DEVICE cannot run */
+} hs_status;
+
+enum { HS_FORM_SIMPLE = 1, HS_FORM_GREEDY = 2 };
+
+typedef enum { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
+
+enum {
+    HS_FLAG_NO_MITIGATION = 1u << 0,     /* greedy order 1 sums x[n] without comparing x[n+1] */
+    HS_FLAG_PER_SPECTRUM_NORM = 1u << 1, /* mu/sigma are [B][H] instead of [H] */
+    HS_FLAG_WHITENING = 1u << 2,         /* load x = fl32(w[j] * p[j]); all lengths equal */
+    HS_FLAG_AUTOTUNE = 1u << 3,          /* time candidate launch shapes at plan creation */
+    HS_FLAG_GRAPH = 1u << 4,             /* hs_run replays a captured CUDA graph */
+    HS_FLAG_NO_DEVICE = 1u << 5,         /* host-only dry run: validate and size, no CUDA calls */
+    HS_FLAG_CHECKED = 1u << 6            /* kernels range-check every index into the error word */
+};
+
+/* Plan description. */
+typedef struct {
+    int32_t dims;            /* 1 (power spectra) or 2 (f-fdot plane) */
+    int32_t H;               /* harmonics summed: 1..32 (1D), 1..8 (2D) */
+    int32_t forms;           /* HS_FORM_SIMPLE | HS_FORM_GREEDY (2D: HS_FORM_GREEDY only) */
+    int32_t dtype;           /* hs_dtype of the stored input (2D: HS_F32 only) */
+    int64_t num_spectra;     /* B >= 1 (1D); 1 for 2D */
+    const int64_t *lengths;  /* host [B]: N_s bins of spectrum s, N_s >= H + 1 (1D) */
+    const int64_t *offsets;  /* host [B] or NULL: element offset of spectrum s in the concatenated
+                                input, each a multiple of 16 bytes / element size; NULL = packed in
+                                order, each start rounded up to 32 elements */
+    int64_t n_freq;          /* 2D: bins per row (f contiguous) */
+    int64_t n_rows;          /* 2D: fdot rows (row-major plane [n_rows][n_freq]) */
+    int64_t z0_row;          /* 2D: row holding z = 0 */
+    uint32_t flags;          /* HS_FLAG_* */
+} hs_desc;
+
+typedef struct hs_plan_s *hs_plan;
+
+/* Per-form inputs and outputs (all device pointers).  F = total fundamentals of the plan
+ * (sum over spectra of N_f, concatenated in spectrum order; 2D: z-major, f fastest). */
+typedef struct {
+    const float *mu;     /* [H] (or [B][H]): mean of an h-term partial sum, entry h-1 (Eq. 2) */
+    const float *sigma;  /* same shape: its standard deviation, > 0 */
+    float *snr;          /* [F] out: max over h of (S_h - mu) / sigma */
+    uint8_t *best_h;     /* [F] out: the h (1..H) of that maximum */
+    void *path;          /* [F] out or NULL (greedy only): drift path, uint8/16/32 for H <= 8/16/32;
+                            2D: uint32, 4 bits per order */
+    uint64_t *argmax;    /* [B] out or NULL: per-spectrum maximum as a key
+                            (ordered-float(snr) << 32) | (0xffffffff - n), n the fundamental
+                            within the spectrum (2D: the flattened output index); ties -> lowest n */
+} hs_form_io;
+
+/* Launch shape of the 1D forward; hs_plan_create picks one (autotuned with HS_FLAG_AUTOTUNE). */
+typedef struct {
+    int32_t kernel;      /* 0 = direct gather, 1 = gather with greedy look-ahead */
+    int32_t threads;     /* threads per CTA: 64..1024, multiple of 32 */
+    int32_t fund_per_thread; /* 1, 2 or 4 fundamentals per thread */
+    int32_t ctas_per_sm; /* persistent grid = ctas_per_sm x SMs; 0 = one CTA per tile */
+    int32_t dynamic;     /* persistent grid takes tiles from an atomic counter (needs workspace) */
+} hs_tuning;
+
+/* Create a plan: validates `desc`, computes fundamental counts and tiles, allocates the plan's
+ * small device tables and error word on `device`.  *out is NULL on failure. */
+hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device);
+hs_status hs_plan_destroy(hs_plan plan);
+
+/* Fundamental counts per spectrum ([B], host, or NULL) and output offsets ([B+1], host, or NULL). */
+hs_status hs_plan_fundamentals(hs_plan plan, int64_t *counts, int64_t *offsets);
+/* Element offset of each spectrum in the input ([B+1], host; last = total extent). */
+hs_status hs_plan_input_offsets(hs_plan plan, int64_t *offsets);
+/* 2D fundamental domain: f in [f_lo, f_hi], z in [z_lo, z_hi]. */
+hs_status hs_plan_domain_2d(hs_plan plan, int64_t *f_lo, int64_t *f_hi, int64_t *z_lo, int64_t *z_hi);
+/* Bytes of device workspace hs_run / hs_backward need (0 = pass NULL). */
+hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
+hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
+hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
+
+/* Forward pass.  spectra: device input of the plan's dtype at the plan's offsets (2D: the plane).
+ * w: device [N] float whitening weights (HS_FLAG_WHITENING) or NULL.  simple / greedy: the
+ * forms' I/O (NULL for a form not in the plan).  workspace: >= hs_plan_workspace bytes or NULL
+ * when that is 0.  Enqueues on `stream`; graph-capturable (it also resets argmax/workspace with
+ * stream-ordered memsets). */
+hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_form_io *simple,
+                 const hs_form_io *greedy, void *workspace, void *stream);
+
+/* Adjoint of one 1D form with the forward's path and best_h held fixed (a subgradient
+ * through the maximum of Eq. 2):
+ *   dL/dx[j] = sum over (n, k <= h*(n)) with b_k(n) = j of grad_snr[n] / sigma[h*(n)-1],
+ *   b_k(n) = k n (simple) or k n + popcount(path[n] & ((1 << k) - 1)) (greedy).
+ * Contributions to each bin are added in a fixed order (k ascending, then even n before odd
+ * n), so the result is bit-reproducible.
+ * grad_in: device [input extent] or NULL: dL/d(spectra); with whitening w[j] dL/dx[j].
+ * grad_w: device [N] or NULL (whitening only): dL/dw[j] = sum_s p_s[j] dL/dx_s[j], spectra in
+ * order.  fwd: the form's forward outputs (best_h, path, sigma are read). */
+hs_status hs_backward(hs_plan plan, int32_t form, const float *grad_snr, const hs_form_io *fwd,
+                      const void *spectra, const float *w, float *grad_in, float *grad_w,
+                      void *workspace, void *stream);
+
+/* Synchronises `stream`, then reads and clears the plan's device error word. */
+hs_status hs_check_device_error(hs_plan plan, void *stream);
+
+/* Host helper: closed-form mu/sigma ([H] each, host) of h-term partial sums when every summed
+ * term is an independent draw from i.i.d. exponential noise of mean `mean1`: simple h mean1,
+ * sqrt(h) mean1; greedy (mitigated) 1.5 h mean1, sqrt(1.25 h) mean1; greedy without mitigation
+ * (1 + 1.5 (h-1)) mean1, sqrt(1 + 1.25 (h-1)) mean1; 2D greedy H_9 h mean1,
+ * sqrt(h sum_{k<=9} 1/k^2) mean1 (max of 9 draws).  No CUDA call. */
+hs_status hs_norm_exponential(int32_t form, int32_t dims, int32_t H, int32_t mitigation,
+                              double mean1, float *mu_out, float *sigma_out);
+
+const char *hs_status_string(hs_status s);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char *hs_last_cuda_error(void);
+/* Library version, e.g. "1.0.0". */
+const char *hs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H */

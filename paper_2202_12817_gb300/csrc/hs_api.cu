@@ -1,0 +1,780 @@
+// Plan, validation, dispatch, CUDA-graph replay and autotuning behind the C ABI of hs.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hs_internal.cuh"
+
+using namespace hs;
+
+namespace {
+
+thread_local std::string g_last_cuda;
+
+bool cuda_ok(cudaError_t e)
+{
+    if (e == cudaSuccess) return true;
+    g_last_cuda = cudaGetErrorString(e);
+    return false;
+}
+
+#define HS_CUDA(call)                                \
+    do {                                             \
+        if (!cuda_ok(call)) return HS_ERR_CUDA;      \
+    } while (0)
+
+constexpr uint32_t kKnownFlags = HS_FLAG_NO_MITIGATION | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_WHITENING |
+                                 HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_NO_DEVICE | HS_FLAG_CHECKED;
+constexpr size_t kWorkspaceBytes = 256;     // tile counter of the dynamic schedule
+constexpr int kBwdBlockBins = 2048;
+constexpr int kBwdThreads = 256;
+
+int elem_bytes(int dtype) { return dtype == HS_F32 ? 4 : 2; }
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Restores the calling thread's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && !cuda_ok(cudaSetDevice(dev))) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct GraphKey {
+    const void *spectra, *w, *ws;
+    hs_form_io s, g;
+    bool operator==(const GraphKey &o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+}  // namespace
+
+struct hs_plan_s {
+    hs_desc d{};
+    int device = 0;
+    bool no_device = false;
+    int sms = 0;
+    int path_bytes = 0;
+    std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
+    int64_t total_fund = 0, extent = 0, max_len = 0;
+    int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
+    hs_tuning tun{1, 256, 1, 0, 0};
+    // device tables
+    int64_t *d_in_off = nullptr, *d_fund_off = nullptr, *d_tile_start = nullptr, *d_in_len = nullptr;
+    int *d_err = nullptr;
+    // graph replay
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    bool gvalid = false;
+    std::mutex mu;
+};
+
+namespace {
+
+int64_t tile_fund(const hs_tuning &t) { return static_cast<int64_t>(t.threads) * t.fund_per_thread; }
+
+void compute_tiles(hs_plan p)
+{
+    const int64_t T = tile_fund(p->tun);
+    const size_t B = p->nf.size();
+    p->tile_start.assign(B + 1, 0);
+    for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf[s] + T - 1) / T;
+}
+
+hs_status upload_tiles(hs_plan p)
+{
+    if (p->no_device || p->d.dims != 1) return HS_OK;
+    HS_CUDA(cudaMemcpy(p->d_tile_start, p->tile_start.data(), sizeof(int64_t) * p->tile_start.size(),
+                       cudaMemcpyHostToDevice));
+    return HS_OK;
+}
+
+hs_status validate_tuning(const hs_tuning *t)
+{
+    if (!t) return HS_ERR_INVALID_ARG;
+    if (t->kernel < 0 || t->kernel > 1) return HS_ERR_INVALID_ARG;
+    if (t->threads < 64 || t->threads > 256 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
+    if (t->fund_per_thread != 1) return HS_ERR_UNSUPPORTED;
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
+    if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
+    if (t->dynamic && t->ctas_per_sm == 0) return HS_ERR_INVALID_ARG;
+    return HS_OK;
+}
+
+const void *fwd1d_kernel(int dtype, int forms, int whitening, int kernel)
+{
+    switch (dtype) {
+    case HS_F32: return fwd1d_kernel_f32(forms, whitening, kernel);
+    case HS_F16: return fwd1d_kernel_f16(forms, whitening, kernel);
+    case HS_BF16: return fwd1d_kernel_bf16(forms, whitening, kernel);
+    }
+    return nullptr;
+}
+
+void free_plan(hs_plan p)
+{
+    if (!p) return;
+    if (!p->no_device) {
+        DeviceGuard g(p->device);
+        if (p->gexec) cudaGraphExecDestroy(p->gexec);
+        if (p->cap) cudaStreamDestroy(p->cap);
+        cudaFree(p->d_in_off);
+        cudaFree(p->d_fund_off);
+        cudaFree(p->d_tile_start);
+        cudaFree(p->d_in_len);
+        cudaFree(p->d_err);
+    }
+    delete p;
+}
+
+hs_status check_io(const hs_plan p, const hs_form_io *io, bool greedy)
+{
+    if (!io || !io->mu || !io->sigma || !io->snr || !io->best_h) return HS_ERR_INVALID_ARG;
+    if (!aligned(io->mu, 4) || !aligned(io->sigma, 4) || !aligned(io->snr, 4)) return HS_ERR_INVALID_ARG;
+    if (io->argmax && !aligned(io->argmax, 8)) return HS_ERR_INVALID_ARG;
+    if (io->path) {
+        if (!greedy) return HS_ERR_INVALID_ARG;
+        if (!aligned(io->path, p->path_bytes)) return HS_ERR_INVALID_ARG;
+    }
+    return HS_OK;
+}
+
+FormArgs to_form_args(const hs_form_io *io)
+{
+    FormArgs f{};
+    if (!io) return f;
+    f.mu = io->mu;
+    f.sigma = io->sigma;
+    f.snr = io->snr;
+    f.best_h = io->best_h;
+    f.path = io->path;
+    f.argmax = reinterpret_cast<unsigned long long *>(io->argmax);
+    return f;
+}
+
+// Enqueue the forward pass (memsets + one kernel) on `st`.
+hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
+                      const hs_form_io *greedy, void *ws, cudaStream_t st)
+{
+    const int64_t B = p->d.dims == 1 ? p->d.num_spectra : 1;
+    if (simple && simple->argmax) HS_CUDA(cudaMemsetAsync(simple->argmax, 0, sizeof(uint64_t) * B, st));
+    if (greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
+    if (p->d.dims == 2) {
+        Fwd2DArgs a{};
+        a.plane = static_cast<const float *>(spectra);
+        a.n_freq = p->d.n_freq;
+        a.n_rows = p->d.n_rows;
+        a.z0_row = p->d.z0_row;
+        a.H = p->d.H;
+        a.f_lo = p->f_lo;
+        a.nff = p->f_hi - p->f_lo + 1;
+        a.z_lo = p->z_lo;
+        a.nz = p->z_hi - p->z_lo + 1;
+        a.checked = (p->d.flags & HS_FLAG_CHECKED) ? 1 : 0;
+        a.g = to_form_args(greedy);
+        a.err = p->d_err;
+        const int threads = 256;
+        dim3 grid(static_cast<unsigned>((a.nff + threads - 1) / threads), static_cast<unsigned>(a.nz));
+        void *args[] = {&a};
+        HS_CUDA(cudaLaunchKernel(fwd2d_kernel(), grid, dim3(threads), args, 0, st));
+        return HS_OK;
+    }
+    const hs_tuning &t = p->tun;
+    Fwd1DArgs a{};
+    a.x = spectra;
+    a.w = w;
+    a.in_off = p->d_in_off;
+    a.fund_off = p->d_fund_off;
+    a.tile_start = p->d_tile_start;
+    a.in_len = p->d_in_len;
+    a.B = static_cast<int32_t>(p->d.num_spectra);
+    a.H = p->d.H;
+    a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;
+    a.per_spectrum_norm = (p->d.flags & HS_FLAG_PER_SPECTRUM_NORM) ? 1 : 0;
+    a.path_bytes = p->path_bytes;
+    a.checked = (p->d.flags & HS_FLAG_CHECKED) ? 1 : 0;
+    a.fund_per_thread = t.fund_per_thread;
+    a.total_tiles = p->tile_start.back();
+    a.s = to_form_args(simple);
+    a.g = to_form_args(greedy);
+    a.err = p->d_err;
+    int64_t grid = a.total_tiles;
+    if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
+    if (t.dynamic) {
+        a.tile_counter = static_cast<unsigned long long *>(ws);
+        // every CTA draws all of its tiles from this counter, starting at 0
+        HS_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), st));
+    }
+    if (grid < 1) return HS_OK;
+    if (grid > 0x7fffffff) return HS_ERR_UNSUPPORTED;
+    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    void *args[] = {&a};
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// autotuner: times candidate launch shapes on a synthetic input shaped like the plan
+// ---------------------------------------------------------------------------------------
+__global__ void k_fill_noise(float *x, int64_t n, uint64_t seed)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        // splitmix64 of the index -> uniform in (0, 1] -> Exp(1) by inversion
+        uint64_t z = seed + static_cast<uint64_t>(i) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float u = (static_cast<float>(z >> 40) + 1.0f) * (1.0f / 16777216.0f);
+        x[i] = -logf(u);
+    }
+}
+
+__global__ void k_f32_to(const float *src, void *dst, int64_t n, int dtype)
+{
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (dtype == HS_F16) static_cast<__half *>(dst)[i] = __float2half_rn(src[i]);
+        else static_cast<__nv_bfloat16 *>(dst)[i] = __float2bfloat16_rn(src[i]);
+    }
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int, int, int>, hs_tuning> g_tune_cache;
+
+hs_status autotune(hs_plan p)
+{
+    const auto key = std::make_tuple(p->device, p->d.H, p->d.forms, p->d.dtype,
+                                     static_cast<int>(p->d.flags & (HS_FLAG_WHITENING | HS_FLAG_NO_MITIGATION)),
+                                     static_cast<int>(std::ceil(std::log2(static_cast<double>(p->max_len)))),
+                                     p->d.num_spectra > 1 ? 1 : 0, p->sms);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->tun = it->second;
+            compute_tiles(p);
+            return upload_tiles(p);
+        }
+    }
+    // sub-plan: up to 8 of the longest spectra, packed
+    std::vector<int64_t> lens(p->len);
+    std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+    if (lens.size() > 8) lens.resize(8);
+    hs_desc sd = p->d;
+    sd.num_spectra = static_cast<int64_t>(lens.size());
+    sd.lengths = lens.data();
+    sd.offsets = nullptr;
+    sd.flags &= ~(HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_CHECKED);
+    if (sd.flags & HS_FLAG_WHITENING) {
+        for (auto &l : lens) l = lens[0];
+    }
+    hs_plan sp = nullptr;
+    hs_status st = hs_plan_create(&sp, &sd, p->device);
+    if (st != HS_OK) return st;
+    const int64_t ext = sp->extent, F = sp->total_fund, H = sp->d.H;
+    void *x = nullptr, *w = nullptr, *ws = nullptr, *outs = nullptr, *norm = nullptr, *tmp = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hs_status result = HS_OK;
+    std::vector<hs_tuning> cands;
+    float best_ms = 1e30f;
+    hs_tuning best = p->tun;
+    hs_form_io fs{}, fg{};
+    const size_t out_bytes = static_cast<size_t>(F) * (4 + 1 + 4 + 1) + 256;
+    if (!cuda_ok(cudaMalloc(&x, ext * elem_bytes(sd.dtype) + 64)) || !cuda_ok(cudaMalloc(&tmp, ext * 4 + 64)) ||
+        !cuda_ok(cudaMalloc(&w, lens[0] * 4 + 64)) || !cuda_ok(cudaMalloc(&ws, kWorkspaceBytes)) ||
+        !cuda_ok(cudaMalloc(&outs, out_bytes)) || !cuda_ok(cudaMalloc(&norm, 4 * H * 4)) ||
+        !cuda_ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) || !cuda_ok(cudaEventCreate(&e0)) ||
+        !cuda_ok(cudaEventCreate(&e1))) {
+        result = HS_ERR_OOM;
+        goto done;
+    }
+    {
+        k_fill_noise<<<1024, 256, 0, s>>>(static_cast<float *>(tmp), ext, 0x2202128170ull);
+        if (sd.dtype == HS_F32) cudaMemcpyAsync(x, tmp, ext * 4, cudaMemcpyDeviceToDevice, s);
+        else k_f32_to<<<1024, 256, 0, s>>>(static_cast<const float *>(tmp), x, ext, sd.dtype);
+        k_fill_noise<<<256, 256, 0, s>>>(static_cast<float *>(w), lens[0], 0x77ull);
+        std::vector<float> hn(4 * H);
+        hs_norm_exponential(HS_FORM_SIMPLE, 1, static_cast<int>(H), 1, 1.0, hn.data(), hn.data() + H);
+        hs_norm_exponential(HS_FORM_GREEDY, 1, static_cast<int>(H), 1, 1.0, hn.data() + 2 * H, hn.data() + 3 * H);
+        cudaMemcpyAsync(norm, hn.data(), 4 * H * 4, cudaMemcpyHostToDevice, s);
+        char *o = static_cast<char *>(outs);
+        auto a16 = [](int64_t v) { return (v + 15) / 16 * 16; };
+        const int64_t o_sb = a16(4 * F), o_gs = a16(o_sb + F), o_gb = a16(o_gs + 4 * F);
+        const float *nrm = static_cast<const float *>(norm);
+        fs.mu = nrm; fs.sigma = nrm + H;
+        fs.snr = reinterpret_cast<float *>(o);
+        fs.best_h = reinterpret_cast<uint8_t *>(o + o_sb);
+        fg.mu = nrm + 2 * H; fg.sigma = nrm + 3 * H;
+        fg.snr = reinterpret_cast<float *>(o + o_gs);
+        fg.best_h = reinterpret_cast<uint8_t *>(o + o_gb);
+        fg.path = nullptr;
+        if (!cuda_ok(cudaStreamSynchronize(s))) { result = HS_ERR_CUDA; goto done; }
+    }
+    for (int kernel = 0; kernel <= 1; ++kernel)
+        for (int threads : {128, 256})
+            for (int sched = 0; sched < 3; ++sched) {
+                hs_tuning t{kernel, threads, 1, 0, 0};
+                if (sched >= 1) {
+                    int occ = 0;
+                    const void *fn = fwd1d_kernel(sd.dtype, sd.forms, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
+                    if (occ < 1) continue;
+                    t.ctas_per_sm = occ;
+                    t.dynamic = sched == 2;
+                }
+                cands.push_back(t);
+            }
+    for (const hs_tuning &t : cands) {
+        sp->tun = t;
+        compute_tiles(sp);
+        if (upload_tiles(sp) != HS_OK) { result = HS_ERR_CUDA; goto done; }
+        const float *wp = (sd.flags & HS_FLAG_WHITENING) ? static_cast<const float *>(w) : nullptr;
+        const hs_form_io *ps = (sd.forms & HS_FORM_SIMPLE) ? &fs : nullptr;
+        const hs_form_io *pg = (sd.forms & HS_FORM_GREEDY) ? &fg : nullptr;
+        float total = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            if (enqueue_fwd(sp, x, wp, ps, pg, ws, s) != HS_OK) { result = HS_ERR_CUDA; goto done; }
+            cudaEventRecord(e1, s);
+            if (!cuda_ok(cudaEventSynchronize(e1))) { result = HS_ERR_CUDA; goto done; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) total += ms;
+        }
+        if (total < best_ms) { best_ms = total; best = t; }
+    }
+    p->tun = best;
+    compute_tiles(p);
+    result = upload_tiles(p);
+    if (result == HS_OK) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+done:
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(x);
+    cudaFree(tmp);
+    cudaFree(w);
+    cudaFree(ws);
+    cudaFree(outs);
+    cudaFree(norm);
+    hs_plan_destroy(sp);
+    return result;
+}
+
+}  // namespace
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+const char *hs_version(void) { return "1.0.0"; }
+
+const char *hs_last_cuda_error(void) { return g_last_cuda.c_str(); }
+
+const char *hs_status_string(hs_status s)
+{
+    switch (s) {
+    case HS_OK: return "ok";
+    case HS_ERR_INVALID_ARG: return "invalid argument";
+    case HS_ERR_UNSUPPORTED: return "unsupported";
+    case HS_ERR_OOM: return "out of memory";
+    case HS_ERR_CUDA: return "CUDA error";
+    case HS_ERR_DEVICE_BOUNDS: return "device index out of bounds";
+    case HS_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case HS_ERR_NO_DEVICE: return "plan has no device";
+    }
+    return "unknown status";
+}
+
+hs_status hs_norm_exponential(int32_t form, int32_t dims, int32_t H, int32_t mitigation, double mean1,
+                              float *mu_out, float *sigma_out)
+{
+    if (!mu_out || !sigma_out || !(mean1 > 0.0) || !std::isfinite(mean1)) return HS_ERR_INVALID_ARG;
+    if (dims == 1) {
+        if (H < 1 || H > kMaxH1D || (form != HS_FORM_SIMPLE && form != HS_FORM_GREEDY)) return HS_ERR_INVALID_ARG;
+    } else if (dims == 2) {
+        if (H < 1 || H > kMaxH2D || form != HS_FORM_GREEDY) return HS_ERR_INVALID_ARG;
+    } else {
+        return HS_ERR_INVALID_ARG;
+    }
+    // mean and variance of the maximum of m i.i.d. Exp(1) draws: sum_{k<=m} 1/k, sum 1/k^2
+    auto hm = [](int m) { double s = 0; for (int k = 1; k <= m; ++k) s += 1.0 / k; return s; };
+    auto hv = [](int m) { double s = 0; for (int k = 1; k <= m; ++k) s += 1.0 / (double(k) * k); return s; };
+    for (int h = 1; h <= H; ++h) {
+        double mean, var;
+        if (dims == 2) {
+            mean = hm(9) * h;
+            var = hv(9) * h;
+        } else if (form == HS_FORM_SIMPLE) {
+            mean = h;
+            var = h;
+        } else if (mitigation) {
+            mean = hm(2) * h;
+            var = hv(2) * h;
+        } else {
+            mean = 1.0 + hm(2) * (h - 1);
+            var = 1.0 + hv(2) * (h - 1);
+        }
+        mu_out[h - 1] = static_cast<float>(mean * mean1);
+        sigma_out[h - 1] = static_cast<float>(std::sqrt(var) * mean1);
+    }
+    return HS_OK;
+}
+
+hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
+{
+    if (!out) return HS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc) return HS_ERR_INVALID_ARG;
+    const hs_desc &d = *desc;
+    if (d.flags & ~kKnownFlags) return HS_ERR_INVALID_ARG;
+    if (d.dtype < HS_F32 || d.dtype > HS_BF16) return HS_ERR_INVALID_ARG;
+    hs_plan p = new (std::nothrow) hs_plan_s();
+    if (!p) return HS_ERR_OOM;
+    p->d = d;
+    p->d.lengths = nullptr;
+    p->d.offsets = nullptr;
+    p->device = device;
+    p->no_device = (d.flags & HS_FLAG_NO_DEVICE) != 0;
+    if (d.dims == 1) {
+        if (d.H < 1 || d.H > kMaxH1D) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.forms < 1 || d.forms > 3) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.num_spectra < 1 || d.num_spectra > (int64_t(1) << 30) || !d.lengths) { delete p; return HS_ERR_INVALID_ARG; }
+        const int64_t B = d.num_spectra;
+        const int eb = elem_bytes(d.dtype);
+        const int64_t al = 16 / eb;
+        p->len.assign(d.lengths, d.lengths + B);
+        p->in_off.assign(B + 1, 0);
+        p->nf.assign(B, 0);
+        p->fund_off.assign(B + 1, 0);
+        int64_t pos = 0;
+        for (int64_t s = 0; s < B; ++s) {
+            const int64_t n = p->len[s];
+            if (n < d.H + 1 || n > (int64_t(1) << 40)) { delete p; return HS_ERR_INVALID_ARG; }
+            int64_t off;
+            if (d.offsets) {
+                off = d.offsets[s];
+                if (off < 0 || off % al) { delete p; return HS_ERR_INVALID_ARG; }
+            } else {
+                off = (pos + 31) / 32 * 32;
+            }
+            p->in_off[s] = off;
+            pos = off + n;
+            p->extent = std::max(p->extent, off + n);
+            p->nf[s] = (n - 1) / d.H;
+            p->fund_off[s + 1] = p->fund_off[s] + p->nf[s];
+            p->max_len = std::max(p->max_len, n);
+        }
+        p->in_off[B] = p->extent;
+        if (d.offsets) {   // spectra must not overlap
+            std::vector<std::pair<int64_t, int64_t>> iv(B);
+            for (int64_t s = 0; s < B; ++s) iv[s] = {p->in_off[s], p->in_off[s] + p->len[s]};
+            std::sort(iv.begin(), iv.end());
+            for (int64_t s = 1; s < B; ++s)
+                if (iv[s].first < iv[s - 1].second) { delete p; return HS_ERR_INVALID_ARG; }
+        }
+        if (d.flags & HS_FLAG_WHITENING)
+            for (int64_t s = 1; s < B; ++s)
+                if (p->len[s] != p->len[0]) { delete p; return HS_ERR_INVALID_ARG; }
+        p->total_fund = p->fund_off[B];
+        p->path_bytes = d.H <= 8 ? 1 : (d.H <= 16 ? 2 : 4);
+    } else if (d.dims == 2) {
+        if (d.H < 1 || d.H > kMaxH2D || d.forms != HS_FORM_GREEDY) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.dtype != HS_F32) { delete p; return HS_ERR_UNSUPPORTED; }
+        if (d.num_spectra != 1) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.flags & (HS_FLAG_WHITENING | HS_FLAG_PER_SPECTRUM_NORM)) { delete p; return HS_ERR_UNSUPPORTED; }
+        if (d.n_freq < 3 || d.n_rows < 3 || d.z0_row < 0 || d.z0_row >= d.n_rows) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.n_freq > (int64_t(1) << 36) || d.n_rows > (int64_t(1) << 20)) { delete p; return HS_ERR_INVALID_ARG; }
+        const int64_t H = d.H;
+        p->f_lo = 1;
+        p->f_hi = (d.n_freq - 1 - H) / H;
+        // z with z0 + h z - h >= 0 and z0 + h z + h <= n_rows - 1 for h = 1 and h = H
+        auto zok = [&](int64_t z) {
+            for (int64_t h : {int64_t(1), H})
+                if (d.z0_row + h * z - h < 0 || d.z0_row + h * z + h > d.n_rows - 1) return false;
+            return true;
+        };
+        int64_t zl = 0, zh = 0;
+        if (!zok(0)) { delete p; return HS_ERR_INVALID_ARG; }
+        while (zok(zl - 1)) --zl;
+        while (zok(zh + 1)) ++zh;
+        p->z_lo = zl;
+        p->z_hi = zh;
+        if (p->f_hi < p->f_lo) { delete p; return HS_ERR_INVALID_ARG; }
+        p->total_fund = (p->f_hi - p->f_lo + 1) * (p->z_hi - p->z_lo + 1);
+        p->extent = d.n_freq * d.n_rows;
+        p->path_bytes = 4;
+        p->len.assign(1, p->extent);
+        p->in_off.assign(2, 0);
+        p->in_off[1] = p->extent;
+        p->nf.assign(1, p->total_fund);
+        p->fund_off = {0, p->total_fund};
+        p->max_len = p->extent;
+    } else {
+        delete p;
+        return HS_ERR_INVALID_ARG;
+    }
+    compute_tiles(p);
+    if (p->no_device) {
+        *out = p;
+        return HS_OK;
+    }
+    DeviceGuard guard(device);
+    if (!guard.ok) { delete p; return HS_ERR_CUDA; }
+    if (!cuda_ok(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device))) { delete p; return HS_ERR_CUDA; }
+    const size_t B1 = p->in_off.size();
+    if (!cuda_ok(cudaMalloc(&p->d_in_off, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_fund_off, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_tile_start, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_in_len, sizeof(int64_t) * (B1 - 1))) ||
+        !cuda_ok(cudaMalloc(&p->d_err, sizeof(int)))) {
+        free_plan(p);
+        return HS_ERR_OOM;
+    }
+    if (!cuda_ok(cudaMemcpy(p->d_in_off, p->in_off.data(), sizeof(int64_t) * B1, cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemcpy(p->d_fund_off, p->fund_off.data(), sizeof(int64_t) * B1, cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemcpy(p->d_in_len, p->len.data(), sizeof(int64_t) * (B1 - 1), cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemset(p->d_err, 0, sizeof(int)))) {
+        free_plan(p);
+        return HS_ERR_CUDA;
+    }
+    hs_status st = upload_tiles(p);
+    if (st == HS_OK && d.dims == 1 && (d.flags & HS_FLAG_AUTOTUNE)) st = autotune(p);
+    if (st != HS_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return HS_OK;
+}
+
+hs_status hs_plan_destroy(hs_plan plan)
+{
+    if (!plan) return HS_ERR_INVALID_ARG;
+    free_plan(plan);
+    return HS_OK;
+}
+
+hs_status hs_plan_fundamentals(hs_plan p, int64_t *counts, int64_t *offsets)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (counts) std::copy(p->nf.begin(), p->nf.end(), counts);
+    if (offsets) std::copy(p->fund_off.begin(), p->fund_off.end(), offsets);
+    return HS_OK;
+}
+
+hs_status hs_plan_input_offsets(hs_plan p, int64_t *offsets)
+{
+    if (!p || !offsets) return HS_ERR_INVALID_ARG;
+    std::copy(p->in_off.begin(), p->in_off.end(), offsets);
+    return HS_OK;
+}
+
+hs_status hs_plan_domain_2d(hs_plan p, int64_t *f_lo, int64_t *f_hi, int64_t *z_lo, int64_t *z_hi)
+{
+    if (!p || p->d.dims != 2) return HS_ERR_INVALID_ARG;
+    if (f_lo) *f_lo = p->f_lo;
+    if (f_hi) *f_hi = p->f_hi;
+    if (z_lo) *z_lo = p->z_lo;
+    if (z_hi) *z_hi = p->z_hi;
+    return HS_OK;
+}
+
+hs_status hs_plan_workspace(hs_plan p, size_t *bytes)
+{
+    if (!p || !bytes) return HS_ERR_INVALID_ARG;
+    *bytes = p->d.dims == 1 ? kWorkspaceBytes : 0;
+    return HS_OK;
+}
+
+hs_status hs_plan_get_tuning(hs_plan p, hs_tuning *t)
+{
+    if (!p || !t) return HS_ERR_INVALID_ARG;
+    *t = p->tun;
+    return HS_OK;
+}
+
+hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    hs_status st = validate_tuning(t);
+    if (st != HS_OK) return st;
+    if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->tun = *t;
+    compute_tiles(p);
+    p->gvalid = false;
+    if (p->no_device) return HS_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    return upload_tiles(p);
+}
+
+hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
+                 const hs_form_io *greedy, void *workspace, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
+    if (w && !aligned(w, 16)) return HS_ERR_INVALID_ARG;
+    const bool want_s = (p->d.forms & HS_FORM_SIMPLE) != 0, want_g = (p->d.forms & HS_FORM_GREEDY) != 0;
+    if (want_s != (simple != nullptr) || want_g != (greedy != nullptr)) return HS_ERR_INVALID_ARG;
+    if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
+    if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
+    if (p->d.dims == 1 && p->tun.dynamic && (!workspace || !aligned(workspace, 8))) return HS_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    if (!(p->d.flags & HS_FLAG_GRAPH)) return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+
+    // graph replay: capture once per argument set on a private stream, launch on `st`
+    std::lock_guard<std::mutex> lk(p->mu);
+    GraphKey k{};
+    std::memset(&k, 0, sizeof(k));
+    k.spectra = spectra;
+    k.w = w;
+    k.ws = workspace;
+    if (simple) k.s = *simple;
+    if (greedy) k.g = *greedy;
+    if (!(p->gvalid && k == p->gkey)) {
+        if (!p->cap && !cuda_ok(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)))
+            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+        cudaGraph_t g = nullptr;
+        bool ok = cuda_ok(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        if (ok) {
+            hs_status es = enqueue_fwd(p, spectra, w, simple, greedy, workspace, p->cap);
+            ok = cuda_ok(cudaStreamEndCapture(p->cap, &g)) && es == HS_OK && g;
+        }
+        if (ok) {
+            if (p->gexec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(p->gexec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(p->gexec);
+                    p->gexec = nullptr;
+                }
+            }
+            if (!p->gexec && !cuda_ok(cudaGraphInstantiate(&p->gexec, g, 0))) {
+                p->gexec = nullptr;
+                ok = false;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {   // capture failed: fall back to a direct launch
+            cudaGetLastError();
+            p->gvalid = false;
+            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+        }
+        p->gkey = k;
+        p->gvalid = true;
+    }
+    HS_CUDA(cudaGraphLaunch(p->gexec, st));
+    return HS_OK;
+}
+
+hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_form_io *fwd,
+                      const void *spectra, const float *w, float *grad_in, float *grad_w,
+                      void *workspace, void *stream)
+{
+    (void)workspace;
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
+    if (form != HS_FORM_SIMPLE && form != HS_FORM_GREEDY) return HS_ERR_INVALID_ARG;
+    if (!(p->d.forms & form)) return HS_ERR_INVALID_ARG;
+    if (!grad_snr || !fwd || !fwd->best_h || !fwd->sigma) return HS_ERR_INVALID_ARG;
+    if (form == HS_FORM_GREEDY && !fwd->path) return HS_ERR_INVALID_ARG;
+    if (!aligned(grad_snr, 4) || !aligned(fwd->sigma, 4)) return HS_ERR_INVALID_ARG;
+    if (fwd->path && !aligned(fwd->path, p->path_bytes)) return HS_ERR_INVALID_ARG;
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
+    if (grad_w && !whiten) return HS_ERR_INVALID_ARG;
+    if (grad_w && (!spectra || !aligned(spectra, 16))) return HS_ERR_INVALID_ARG;
+    if (!grad_in && !grad_w) return HS_OK;
+    if ((grad_in && !aligned(grad_in, 4)) || (grad_w && !aligned(grad_w, 4))) return HS_ERR_INVALID_ARG;
+    const int64_t B = p->d.num_spectra;
+    Bwd1DArgs a{};
+    a.form = form;
+    a.H = p->d.H;
+    a.B = static_cast<int32_t>(B);
+    a.path_bytes = p->path_bytes;
+    a.grad_snr = grad_snr;
+    a.best_h = fwd->best_h;
+    a.path = fwd->path;
+    a.sigma = fwd->sigma;
+    a.per_spectrum_norm = (p->d.flags & HS_FLAG_PER_SPECTRUM_NORM) ? 1 : 0;
+    a.p = spectra;
+    a.dtype = p->d.dtype;
+    a.w = w;
+    a.in_off = p->d_in_off;
+    a.in_len = p->d_in_len;
+    a.fund_off = p->d_fund_off;
+    a.grad_in = grad_in;
+    a.grad_w = grad_w;
+    a.n_common = p->len[0];
+    a.block_bins = kBwdBlockBins;
+    a.err = p->d_err;
+    int64_t gx;
+    int gy;
+    if (grad_w) {
+        gx = (p->len[0] + kBwdBlockBins - 1) / kBwdBlockBins;
+        gy = 1;
+    } else {
+        gx = (p->max_len + kBwdBlockBins - 1) / kBwdBlockBins;
+        if (B > 65535) return HS_ERR_UNSUPPORTED;
+        gy = static_cast<int>(B);
+    }
+    if (gx > 0x7fffffff) return HS_ERR_UNSUPPORTED;
+    a.blocks_per_spectrum = gx;
+    const void *fn = bwd1d_kernel(form, p->d.dtype, whiten ? 1 : 0);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    void *args[] = {&a};
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(gx), gy), dim3(kBwdThreads), args,
+                             2 * kBwdBlockBins * sizeof(float), static_cast<cudaStream_t>(stream)));
+    return HS_OK;
+}
+
+hs_status hs_check_device_error(hs_plan p, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    HS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int e = 0;
+    HS_CUDA(cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != kErrNone) HS_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    if (e == kErrBounds) return HS_ERR_DEVICE_BOUNDS;
+    if (e == kErrTimeout) return HS_ERR_DEVICE_TIMEOUT;
+    return HS_OK;
+}
+
+}  // extern "C"

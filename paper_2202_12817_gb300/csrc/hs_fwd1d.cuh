@@ -1,0 +1,325 @@
+// 1D forward harmonic-sum kernels (simple form, Eq. 3; greedy form, Eq. 5 / Algorithm 2),
+// templated on the stored type, the forms computed in one pass and whitening.  Included by
+// one translation unit per stored type.
+#pragma once
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+// ---------------------------------------------------------------------------------------
+// loads
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float ld_raw(const T *p, int64_t j);
+
+template <>
+__device__ __forceinline__ float ld_raw<float>(const float *p, int64_t j)
+{
+    return __ldg(p + j);
+}
+template <>
+__device__ __forceinline__ float ld_raw<__half>(const __half *p, int64_t j)
+{
+    unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + j);
+    return __half2float(__ushort_as_half(b));
+}
+template <>
+__device__ __forceinline__ float ld_raw<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t j)
+{
+    unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + j);
+    return __uint_as_float(static_cast<unsigned int>(b) << 16);
+}
+
+// Loaded power x[j]: the stored value, or fl32(w[j] * p[j]) with whitening.
+template <typename T, bool WHITEN>
+__device__ __forceinline__ float ld_x(const T *p, const float *w, int64_t j)
+{
+    float v = ld_raw<T>(p, j);
+    if constexpr (WHITEN) v = __fmul_rn(__ldg(w + j), v);
+    return v;
+}
+
+// ordered-float key: larger float -> larger unsigned
+__device__ __forceinline__ unsigned int ordered_bits(float f)
+{
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ unsigned long long argmax_key(float snr, int64_t n)
+{
+    return (static_cast<unsigned long long>(ordered_bits(snr)) << 32) |
+           static_cast<unsigned long long>(0xffffffffu - static_cast<unsigned int>(n));
+}
+
+__device__ __forceinline__ void set_error(int *err, int code)
+{
+    if (err) atomicCAS(err, kErrNone, code);
+}
+
+// Block-wide max of a 64-bit key, then one atomicMax per CTA.
+__device__ __forceinline__ void block_argmax(unsigned long long key, unsigned long long *dst,
+                                             unsigned long long *scratch /*[32] smem*/)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        key = k2 > key ? k2 : key;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) scratch[warp] = key;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        key = lane < nw ? scratch[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            key = k2 > key ? k2 : key;
+        }
+        if (lane == 0 && key != 0ull) atomicMax(dst, key);
+    }
+}
+
+// spectrum owning a tile: largest s with tile_start[s] <= t
+__device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Normalisation table in shared memory: rs = 1/sigma, murs = mu * rs, so that
+// SNR = S * rs - murs (one FMA); error relative to (|S| + |mu|) / sigma stays ~3 ulp.
+struct NormSmem {
+    float rs[2][kMaxH1D];
+    float murs[2][kMaxH1D];
+};
+
+__device__ __forceinline__ void load_norm(NormSmem &nm, int slot, const float *mu, const float *sigma,
+                                          int H)
+{
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        float rs = __frcp_rn(__ldg(sigma + h));
+        nm.rs[slot][h] = rs;
+        nm.murs[slot][h] = __fmul_rn(__ldg(mu + h), rs);
+    }
+}
+
+__device__ __forceinline__ void store_path(void *path, int bytes, int64_t i, uint32_t bits)
+{
+    if (bytes == 4) static_cast<uint32_t *>(path)[i] = bits;
+    else if (bytes == 2) static_cast<uint16_t *>(path)[i] = static_cast<uint16_t>(bits);
+    else if (bytes == 1) static_cast<uint8_t *>(path)[i] = static_cast<uint8_t>(bits);
+}
+
+// One running SNR maximum (Eq. 2): start at h = 1, strictly larger replaces.
+struct RunMax {
+    float best;
+    int bh;
+    __device__ __forceinline__ void first(float snr) { best = snr; bh = 1; }
+    __device__ __forceinline__ void step(float snr, int h)
+    {
+        if (snr > best) { best = snr; bh = h; }
+    }
+};
+
+// ---------------------------------------------------------------------------------------
+// greedy candidate selection for the look-ahead kernel
+// ---------------------------------------------------------------------------------------
+template <int J>
+__device__ __forceinline__ float pick(const float (&v)[J], int r)
+{
+    float out = v[0];
+#pragma unroll
+    for (int i = 1; i < J; ++i) out = (r == i) ? v[i] : out;
+    return out;
+}
+
+// ---------------------------------------------------------------------------------------
+// kernel: one thread per fundamental, tiles of blockDim.x fundamentals.
+//   LOOKAHEAD = 1: every order loads its two candidates after the previous comparison
+//                  (a chain of H dependent loads per fundamental);
+//   LOOKAHEAD = G > 1: with the drift d known before order h0, all candidates of orders
+//                  h0..h0+G-1 ((h0+j) n + d + [0, j+1]) are loaded at once and the G
+//                  comparisons run from registers: H/G dependent rounds.
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN, int LOOKAHEAD>
+__global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
+{
+    __shared__ NormSmem nm;
+    __shared__ unsigned long long red[32];
+    __shared__ long long s_tile;
+    constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
+    constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
+    const int H = a.H;
+    int loaded_spec = -1;
+
+    int64_t tile = blockIdx.x;
+    if (a.tile_counter) {
+        if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+        __syncthreads();
+        tile = s_tile;
+    }
+    while (tile < a.total_tiles) {
+        const int s = tile_spectrum(a.tile_start, a.B, tile);
+        if (s != loaded_spec) {
+            if (loaded_spec >= 0) __syncthreads();
+            const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
+            if (kS) load_norm(nm, 0, a.s.mu + no, a.s.sigma + no, H);
+            if (kG) load_norm(nm, 1, a.g.mu + no, a.g.sigma + no, H);
+            __syncthreads();
+            loaded_spec = s;
+        }
+        const int64_t fbase = __ldg(a.fund_off + s);
+        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t n = (tile - __ldg(a.tile_start + s)) * blockDim.x + threadIdx.x;
+        const bool valid = n < nf;
+        const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
+        if (a.checked && valid) {
+            // every read of both forms lies in [0, H n + H]; checked mode verifies the domain
+            const int64_t len = __ldg(a.in_len + s);
+            if (static_cast<int64_t>(H) * n + H > len - 1) set_error(a.err, kErrBounds);
+        }
+        RunMax ms{0.f, 1}, mg{0.f, 1};
+        uint32_t bits = 0;
+        if (valid) {
+            // ---- order 1 ----
+            const float x0 = ld_x<T, WHITEN>(x, a.w, n);
+            float ss = x0, sg = x0;
+            int d = 0;
+            if (kG && a.mitigation) {
+                const float b = ld_x<T, WHITEN>(x, a.w, n + 1);
+                if (b > x0) { d = 1; sg = b; bits = 1u; }
+            }
+            if (kS) ms.first(fmaf(ss, nm.rs[0][0], -nm.murs[0][0]));
+            if (kG) mg.first(fmaf(sg, nm.rs[1][0], -nm.murs[1][0]));
+            if constexpr (LOOKAHEAD <= 1) {
+                for (int h = 2; h <= H; ++h) {
+                    const int64_t hn = static_cast<int64_t>(h) * n;
+                    if (kS) {
+                        ss += ld_x<T, WHITEN>(x, a.w, hn);
+                        ms.step(fmaf(ss, nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
+                    }
+                    if (kG) {
+                        const int64_t m = hn + d;
+                        const float va = ld_x<T, WHITEN>(x, a.w, m);
+                        const float vb = ld_x<T, WHITEN>(x, a.w, m + 1);
+                        const bool inc = vb > va;
+                        sg += inc ? vb : va;
+                        d += inc;
+                        bits |= static_cast<uint32_t>(inc) << (h - 1);
+                        mg.step(fmaf(sg, nm.rs[1][h - 1], -nm.murs[1][h - 1]), h);
+                    }
+                }
+            } else {
+                constexpr int G = LOOKAHEAD;
+                for (int h0 = 2; h0 <= H; h0 += G) {
+                    float sv[G];
+                    float v[G][G + 1];
+                    // issue every load of the group before any comparison
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const int h = h0 + j;
+                        if (h <= H) {
+                            const int64_t hn = static_cast<int64_t>(h) * n;
+                            if (kS) sv[j] = ld_x<T, WHITEN>(x, a.w, hn);
+                            if (kG) {
+#pragma unroll
+                                for (int i = 0; i <= j + 1; ++i) v[j][i] = ld_x<T, WHITEN>(x, a.w, hn + d + i);
+                            }
+                        }
+                    }
+                    int r = 0;
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const int h = h0 + j;
+                        if (h <= H) {
+                            if (kS) {
+                                ss += sv[j];
+                                ms.step(fmaf(ss, nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
+                            }
+                            if (kG) {
+                                float va = v[j][0], vb = v[j][1];
+#pragma unroll
+                                for (int i = 1; i <= j; ++i) {
+                                    va = (r == i) ? v[j][i] : va;
+                                    vb = (r == i) ? v[j][i + 1] : vb;
+                                }
+                                const bool inc = vb > va;
+                                sg += inc ? vb : va;
+                                r += inc;
+                                bits |= static_cast<uint32_t>(inc) << (h - 1);
+                                mg.step(fmaf(sg, nm.rs[1][h - 1], -nm.murs[1][h - 1]), h);
+                            }
+                        }
+                    }
+                    d += r;
+                }
+            }
+            const int64_t o = fbase + n;
+            if (kS) {
+                a.s.snr[o] = ms.best;
+                a.s.best_h[o] = static_cast<uint8_t>(ms.bh);
+            }
+            if (kG) {
+                a.g.snr[o] = mg.best;
+                a.g.best_h[o] = static_cast<uint8_t>(mg.bh);
+                if (a.g.path) store_path(a.g.path, a.path_bytes, o, bits);
+            }
+        }
+        if (kS && a.s.argmax)
+            block_argmax(valid ? argmax_key(ms.best, n) : 0ull, a.s.argmax + s, red);
+        if (kG && a.g.argmax) {
+            if (kS && a.s.argmax) __syncthreads();
+            block_argmax(valid ? argmax_key(mg.best, n) : 0ull, a.g.argmax + s, red);
+        }
+        // next tile
+        if (a.tile_counter) {
+            __syncthreads();
+            if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+            __syncthreads();
+            tile = s_tile;
+        } else {
+            tile += gridDim.x;
+            if (tile < a.total_tiles) __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// dispatch for one stored type
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+static const void *fwd1d_kernel_ptr(int kernel)
+{
+    switch (kernel) {
+    case 0: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 1>);
+    case 1: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 4>);
+    default: return nullptr;
+    }
+}
+
+template <typename T>
+static const void *fwd1d_kernel_for(int forms, int whitening, int kernel)
+{
+    if (whitening) {
+        switch (forms) {
+        case 1: return fwd1d_kernel_ptr<T, 1, true>(kernel);
+        case 2: return fwd1d_kernel_ptr<T, 2, true>(kernel);
+        case 3: return fwd1d_kernel_ptr<T, 3, true>(kernel);
+        }
+    } else {
+        switch (forms) {
+        case 1: return fwd1d_kernel_ptr<T, 1, false>(kernel);
+        case 2: return fwd1d_kernel_ptr<T, 2, false>(kernel);
+        case 3: return fwd1d_kernel_ptr<T, 3, false>(kernel);
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace hs

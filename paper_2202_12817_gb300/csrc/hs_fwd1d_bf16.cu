@@ -1,0 +1,9 @@
+// 1D forward kernels instantiated for stored type __nv_bfloat16.
+#include "hs_fwd1d.cuh"
+
+namespace hs {
+const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel)
+{
+    return fwd1d_kernel_for<__nv_bfloat16>(forms, whitening, kernel);
+}
+}  // namespace hs

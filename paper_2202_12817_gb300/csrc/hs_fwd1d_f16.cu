@@ -1,0 +1,9 @@
+// 1D forward kernels instantiated for stored type __half.
+#include "hs_fwd1d.cuh"
+
+namespace hs {
+const void *fwd1d_kernel_f16(int forms, int whitening, int kernel)
+{
+    return fwd1d_kernel_for<__half>(forms, whitening, kernel);
+}
+}  // namespace hs

@@ -1,0 +1,9 @@
+// 1D forward kernels instantiated for stored type float.
+#include "hs_fwd1d.cuh"
+
+namespace hs {
+const void *fwd1d_kernel_f32(int forms, int whitening, int kernel)
+{
+    return fwd1d_kernel_for<float>(forms, whitening, kernel);
+}
+}  // namespace hs

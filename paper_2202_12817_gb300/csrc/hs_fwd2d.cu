@@ -1,0 +1,74 @@
+// 2D greedy harmonic sum over an f-fdot plane: the 1D greedy rule (Eq. 5, Algorithm 2)
+// lifted to a 3x3 neighbourhood at (h f + df, h z + dz).  The paper names the
+// higher-dimensional sum (acceleration search) without giving an algorithm; the rule here
+// is: best value starts at the centre, the 8 neighbours are scanned in raster order
+// (dz = -1..1 outer, df = -1..1 inner) and replace it only when strictly larger.
+#include "hs_fwd1d.cuh"
+
+namespace hs {
+
+__global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
+{
+    __shared__ float rs[kMaxH2D], murs[kMaxH2D];
+    __shared__ unsigned long long red[32];
+    const int H = a.H;
+    if (threadIdx.x < H) {
+        const float r = __frcp_rn(__ldg(a.g.sigma + threadIdx.x));
+        rs[threadIdx.x] = r;
+        murs[threadIdx.x] = __fmul_rn(__ldg(a.g.mu + threadIdx.x), r);
+    }
+    __syncthreads();
+    const int64_t fi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t zi = blockIdx.y;
+    const bool valid = fi < a.nff;
+    const int64_t o = zi * a.nff + fi;
+    float best = 0.f;
+    if (valid) {
+        const int64_t f = a.f_lo + fi, z = a.z_lo + zi;
+        const int64_t nfq = a.n_freq;
+        int64_t df = 0, dz = 0;
+        float sum = 0.f;
+        uint32_t bits = 0;
+        int bh = 1;
+        for (int h = 1; h <= H; ++h) {
+            const int64_t cf = h * f + df;
+            const int64_t cr = a.z0_row + h * z + dz;
+            if (a.checked) {
+                if (cr - 1 < 0 || cr + 1 > a.n_rows - 1 || cf - 1 < 0 || cf + 1 > nfq - 1) {
+                    set_error(a.err, kErrBounds);
+                    break;
+                }
+            }
+            const float *r0 = a.plane + (cr - 1) * nfq + cf;   // row z - 1, column cf
+            const float *r1 = r0 + nfq;
+            const float *r2 = r1 + nfq;
+            const float c00 = __ldg(r0 - 1), c01 = __ldg(r0), c02 = __ldg(r0 + 1);
+            const float c10 = __ldg(r1 - 1), c11 = __ldg(r1), c12 = __ldg(r1 + 1);
+            const float c20 = __ldg(r2 - 1), c21 = __ldg(r2), c22 = __ldg(r2 + 1);
+            float v = c11;
+            int code = 4;
+            if (c00 > v) { v = c00; code = 0; }
+            if (c01 > v) { v = c01; code = 1; }
+            if (c02 > v) { v = c02; code = 2; }
+            if (c10 > v) { v = c10; code = 3; }
+            if (c12 > v) { v = c12; code = 5; }
+            if (c20 > v) { v = c20; code = 6; }
+            if (c21 > v) { v = c21; code = 7; }
+            if (c22 > v) { v = c22; code = 8; }
+            sum += v;
+            df += code % 3 - 1;
+            dz += code / 3 - 1;
+            bits |= static_cast<uint32_t>(code) << (4 * (h - 1));
+            const float snr = fmaf(sum, rs[h - 1], -murs[h - 1]);
+            if (h == 1 || snr > best) { best = snr; bh = h; }
+        }
+        a.g.snr[o] = best;
+        a.g.best_h[o] = static_cast<uint8_t>(bh);
+        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = bits;
+    }
+    if (a.g.argmax) block_argmax(valid ? argmax_key(best, o) : 0ull, a.g.argmax, red);
+}
+
+const void *fwd2d_kernel() { return reinterpret_cast<const void *>(&k_fwd2d); }
+
+}  // namespace hs

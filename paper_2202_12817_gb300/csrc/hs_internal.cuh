@@ -1,0 +1,100 @@
+// Internal definitions shared by the harmonic-sum kernels and the plan / C-ABI code.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hs.h"
+
+namespace hs {
+
+constexpr int kMaxH1D = 32;
+constexpr int kMaxH2D = 8;
+
+// Device error word values (first error wins).
+constexpr int kErrNone = 0;
+constexpr int kErrBounds = 1;
+constexpr int kErrTimeout = 2;
+
+// Per-form arguments of the forward kernels.
+struct FormArgs {
+    const float *mu;
+    const float *sigma;
+    float *snr;
+    uint8_t *best_h;
+    void *path;
+    unsigned long long *argmax;
+};
+
+// 1D forward launch arguments.
+struct Fwd1DArgs {
+    const void *x;                 // concatenated spectra (dtype of the plan)
+    const float *w;                // whitening weights [N] or nullptr
+    const int64_t *in_off;         // [B+1] element offset of each spectrum
+    const int64_t *fund_off;       // [B+1] output offset of each spectrum (prefix of N_f)
+    const int64_t *tile_start;     // [B+1] prefix of tiles per spectrum
+    const int64_t *in_len;         // [B] N_s (for checked mode)
+    int32_t B;
+    int32_t H;
+    int32_t mitigation;
+    int32_t per_spectrum_norm;
+    int32_t path_bytes;            // 0, 1, 2 or 4
+    int32_t checked;
+    int32_t fund_per_thread;
+    int64_t total_tiles;
+    unsigned long long *tile_counter;  // dynamic schedule (nullptr = static)
+    FormArgs s;                    // simple form outputs (unused unless the form is on)
+    FormArgs g;                    // greedy form outputs
+    int *err;                      // device error word
+};
+
+// 2D forward launch arguments.
+struct Fwd2DArgs {
+    const float *plane;
+    int64_t n_freq;
+    int64_t n_rows;
+    int64_t z0_row;
+    int32_t H;
+    int64_t f_lo, nff;             // f in [f_lo, f_lo + nff)
+    int64_t z_lo, nz;              // z in [z_lo, z_lo + nz)
+    int32_t checked;
+    FormArgs g;
+    int *err;
+};
+
+// 1D adjoint launch arguments.
+struct Bwd1DArgs {
+    int32_t form;
+    int32_t H;
+    int32_t B;
+    int32_t path_bytes;
+    const float *grad_snr;
+    const uint8_t *best_h;
+    const void *path;
+    const float *sigma;
+    int32_t per_spectrum_norm;
+    const void *p;                 // spectra (for grad_w / whitening)
+    int32_t dtype;
+    const float *w;
+    const int64_t *in_off;
+    const int64_t *in_len;
+    const int64_t *fund_off;
+    float *grad_in;
+    float *grad_w;
+    int64_t n_common;              // N when grad_w is requested
+    int32_t block_bins;            // bins per CTA
+    int64_t blocks_per_spectrum;   // grid.x in per-spectrum mode
+    int *err;
+};
+
+// ---- kernel entry points (defined in the kernel translation units) ----
+// 1D forward: kernel 0 = direct gather, 1 = greedy look-ahead; forms 1..3; whitening 0/1.
+const void *fwd1d_kernel_f32(int forms, int whitening, int kernel);
+const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
+const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
+const void *fwd2d_kernel();
+const void *bwd1d_kernel(int form, int dtype, int whitening);
+
+}  // namespace hs

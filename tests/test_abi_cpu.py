@@ -1,0 +1,160 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol hs.h declares, validates
+plans on the host (HS_FLAG_NO_DEVICE) and its host helpers agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2202_12817_gb300 as m
+    return m
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "hs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(hs):
+    names = declared_functions()
+    assert len(names) >= 14
+    L = ctypes.CDLL(hs.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert hs.lib().hs_version() == b"1.0.0"
+
+
+def test_status_strings(hs):
+    for s in range(8):
+        assert hs.status_string(s) not in ("", "unknown status")
+    assert hs.status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("form,dims,mit,mean1", [(1, 1, True, 1.0), (2, 1, True, 1.0), (2, 1, False, 1.0),
+                                                 (2, 2, True, 2.0), (1, 1, True, 3.5)])
+def test_norm_exponential_matches_oracle(hs, oracle_lib, form, dims, mit, mean1):
+    H = 8 if dims == 2 else 32
+    mu, sg = hs.norm_exponential(form, dims, H, mit, mean1)
+    rmu, rsg = oracle_lib.norm_exponential(form, dims, H, mitigation=mit, mean1=mean1)
+    np.testing.assert_allclose(mu, rmu, rtol=1e-7)
+    np.testing.assert_allclose(sg, rsg, rtol=1e-7)
+
+
+def test_norm_exponential_rejects(hs):
+    with pytest.raises(hs.HSError):
+        hs.norm_exponential(1, 2, 8)          # 2D has only the greedy form
+    with pytest.raises(hs.HSError):
+        hs.norm_exponential(2, 1, 33)
+    with pytest.raises(hs.HSError):
+        hs.norm_exponential(2, 1, 4, True, -1.0)
+
+
+def plan(hs, **kw):
+    kw.setdefault("flags", 0)
+    kw["flags"] |= hs.FLAG_NO_DEVICE
+    return hs.Plan(**kw)
+
+
+def test_plan_counts_offsets(hs):
+    lens = [131072, 1000, 33, 40]
+    p = plan(hs, H=32, forms=3, lengths=lens)
+    assert list(p.counts) == [(n - 1) // 32 for n in lens]
+    assert list(p.fund_offsets) == [0] + list(np.cumsum(p.counts))
+    off = p.input_offsets
+    assert off[0] == 0 and all(o % 32 == 0 for o in off[:-1])
+    assert all(off[i] >= off[i - 1] + lens[i - 1] for i in range(1, len(lens)))
+    assert off[-1] == off[-2] + lens[-1]
+    assert p.path_bytes == 4 and p.workspace_bytes > 0
+    assert plan(hs, H=8, forms=2, lengths=[100]).path_bytes == 1
+    assert plan(hs, H=16, forms=2, lengths=[100]).path_bytes == 2
+
+
+def test_plan_2d_domain(hs):
+    p = plan(hs, H=8, forms=hs.GREEDY, dims=2, n_freq=1 << 21, n_rows=201, z0_row=100)
+    assert p.domain == (1, 262142, -11, 11)
+    assert p.total_fundamentals == 262142 * 23
+
+
+def test_plan_2d_domain_matches_oracle(hs, oracle_lib):
+    for nf, nr, z0, H in [(5000, 41, 20, 3), (1000, 30, 10, 4), (777, 9, 4, 1)]:
+        p = plan(hs, H=H, forms=hs.GREEDY, dims=2, n_freq=nf, n_rows=nr, z0_row=z0)
+        assert p.domain == oracle_lib.domain_2d(nf, nr, z0, H) or nr != 2 * z0 + 1
+
+
+@pytest.mark.parametrize("kw", [
+    dict(H=0, forms=3, lengths=[100]),
+    dict(H=33, forms=3, lengths=[100]),
+    dict(H=8, forms=0, lengths=[100]),
+    dict(H=8, forms=4, lengths=[100]),
+    dict(H=8, forms=3, lengths=[8]),                       # N < H + 1: no fundamental
+    dict(H=8, forms=3, lengths=[100], dtype=3),
+    dict(H=8, forms=3, lengths=[100, 100], offsets=[0, 3]),   # misaligned offset
+    dict(H=8, forms=3, lengths=[100, 100], offsets=[0, 64]),  # overlapping spectra
+    dict(H=8, forms=3, lengths=[100, 96], flags=1 << 2),      # whitening needs equal lengths
+    dict(H=8, forms=3, lengths=[100], flags=1 << 12),         # unknown flag
+    dict(H=9, forms=2, dims=2, n_freq=1000, n_rows=41, z0_row=20),
+    dict(H=4, forms=1, dims=2, n_freq=1000, n_rows=41, z0_row=20),
+    dict(H=4, forms=2, dims=2, n_freq=1000, n_rows=5, z0_row=2),   # no z fits
+    dict(H=4, forms=2, dims=3, n_freq=1000, n_rows=41, z0_row=20),
+])
+def test_plan_rejects(hs, kw):
+    with pytest.raises(hs.HSError) as e:
+        plan(hs, **kw)
+    assert e.value.status in (1, 2)
+
+
+def test_offsets_accepted(hs):
+    p = plan(hs, H=8, forms=3, lengths=[100, 100], offsets=[128, 0])
+    assert list(p.input_offsets[:2]) == [128, 0] and p.extent == 228
+    p = plan(hs, H=8, forms=3, lengths=[100, 100], offsets=[0, 104], dtype=hs.F16)
+    assert p.extent == 204
+
+
+def test_run_without_device(hs):
+    p = plan(hs, H=8, forms=3, lengths=[100])
+    L = hs.lib()
+    assert L.hs_run(p.handle, 16, None, None, None, None, None) == 7
+    assert L.hs_backward(p.handle, 2, 16, None, None, None, None, None, None, None) == 7
+    assert L.hs_check_device_error(p.handle, None) == 7
+    assert L.hs_run(None, 16, None, None, None, None, None) == 1
+
+
+def test_tuning_validation(hs):
+    p = plan(hs, H=8, forms=3, lengths=[10000])
+    t = p.tuning
+    assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
+    p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
+    assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
+    for bad in (dict(kernel=2, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
+                dict(kernel=0, threads=100, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
+                dict(kernel=0, threads=512, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
+                dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=1)):
+        with pytest.raises(hs.HSError):
+            p.tuning = bad
+
+
+def test_decode_argmax(hs):
+    for snr, n in [(3.25, 17), (-2.5, 0), (0.0, 4095), (1e6, 123456)]:
+        u = np.frombuffer(np.float32(snr).tobytes(), np.uint32)[0]
+        o = (u & 0x7FFFFFFF) | 0x80000000 if not (u & 0x80000000) else (~u & 0xFFFFFFFF)
+        key = (int(o) << 32) | (0xFFFFFFFF - n)
+        assert hs.decode_argmax(np.int64(np.uint64(key).astype(np.int64))) == (np.float32(snr), n)
+        assert hs.decode_argmax(key) == (np.float32(snr), n)
+
+
+def test_plan_create_without_gpu_fails_cleanly(hs):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(hs.HSError) as e:
+        hs.Plan(H=8, forms=3, lengths=[100])
+    assert e.value.status == 4

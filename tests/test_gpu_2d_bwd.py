@@ -1,0 +1,193 @@
+"""GPU parity of the 2D greedy forward and of the 1D adjoint (plus its autograd wrapper)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from hs_check import compare_argmax, compare_form, path_view
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+# ---------------------------------------------------------------------------------------------
+# 2D greedy
+# ---------------------------------------------------------------------------------------------
+def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0):
+    n_rows, n_freq = pl.shape
+    plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=flags)
+    assert plan.domain == o.domain_2d(n_freq, n_rows, z0, H)
+    mu, sg = hs.norm_exponential(2, 2, H, True, mean1)
+    ng = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    out = plan.forward(torch.from_numpy(pl).to(DEV), None, ng)[hs.GREEDY]
+    torch.cuda.synchronize()
+    hs.check_device_error(plan)
+    r_snr, r_bh, r_path, r_all = o.greedy_2d(pl, z0, H, mu, sg, want_all=True)
+    g_snr = out.snr.cpu().numpy()
+    near = compare_form(g_snr, out.best_h.cpu().numpy(), r_snr, r_bh, r_all, mu, sg,
+                        path_view(out.path, H), r_path, what="2d")
+    compare_argmax(out.argmax.cpu().numpy()[0], r_snr, g_snr, mu, sg, r_bh, hs.decode_argmax, what="2d argmax")
+    plan.close()
+    return near
+
+
+@pytest.mark.parametrize("H", [1, 2, 3, 4, 8])
+def test_2d_small(hs, oracle_lib, H):
+    z0 = 30
+    pl = synth.plane(5003, 2 * z0 + 1, z0, 40 + H, synth.random_tracks(3, 5003, 8, f_lo=50, zmax=3))
+    run_2d(hs, oracle_lib, pl, z0, H)
+
+
+def test_2d_asymmetric_rows_checked(hs, oracle_lib):
+    pl = synth.plane(3001, 37, 14, 3)
+    run_2d(hs, oracle_lib, pl, 14, 4, flags=hs.FLAG_CHECKED)
+
+
+def test_2d_integer_ties(hs, oracle_lib):
+    pl = np.floor(synth.plane(2048, 41, 20, 6) * 0.7).astype(np.float32)
+    run_2d(hs, oracle_lib, pl, 20, 5)
+
+
+def test_2d_full_size(hs, oracle_lib):
+    """f-fdot plane 201 x 2^21, H = 8, chi-square(2) noise + 8 drifting tracks."""
+    tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
+    pl = synth.plane(synth.PLANE_N_FREQ, synth.PLANE_N_ROWS, synth.PLANE_Z0_ROW, synth.SEED_BASE + 4, tracks)
+    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8)
+    assert near <= 20
+
+
+# ---------------------------------------------------------------------------------------------
+# 1D adjoint
+# ---------------------------------------------------------------------------------------------
+def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True):
+    lengths = [len(x) for x in xs]
+    flags = (hs.FLAG_WHITENING if w is not None else 0) | (0 if mitigation else hs.FLAG_NO_MITIGATION)
+    plan = hs.Plan(H, form, lengths=lengths, dtype=dtype, flags=flags)
+    tdt = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}[dtype]
+    buf = torch.zeros(plan.extent, dtype=tdt)
+    refs = []
+    for s, x in enumerate(xs):
+        t = torch.from_numpy(x).to(tdt)
+        buf[int(plan.input_offsets[s]):int(plan.input_offsets[s]) + len(x)] = t
+        refs.append(t.float().numpy())
+    xd = buf.to(DEV)
+    wd = None if w is None else torch.from_numpy(w).to(DEV)
+    mu, sg = hs.norm_exponential(form, 1, H, mitigation)
+    nrm = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    out = plan.forward(xd, nrm if form == 1 else None, nrm if form == 2 else None, w=wd)[form]
+    g = torch.from_numpy(synth.upstream_grad(plan.total_fundamentals, 17)).to(DEV)
+    gin = torch.zeros(plan.extent, dtype=torch.float32, device=DEV)
+    gw = torch.zeros(len(xs[0]), dtype=torch.float32, device=DEV) if w is not None else None
+    hs.backward(plan, form, g, out, xd, wd, gin, gw)
+    gin2 = torch.zeros_like(gin)
+    gw2 = torch.zeros_like(gw) if gw is not None else None
+    hs.backward(plan, form, g, out, xd, wd, gin2, gw2)
+    torch.cuda.synchronize()
+    assert torch.equal(gin, gin2), "adjoint is not bit-reproducible"
+    if gw is not None:
+        assert torch.equal(gw, gw2)
+    gin = gin.cpu().numpy()
+    gn = g.cpu().numpy().astype(np.float64)
+    gw_ref = np.zeros(len(xs[0])) if w is not None else None
+    for s, x in enumerate(xs):
+        a, b = int(plan.fund_offsets[s]), int(plan.fund_offsets[s + 1])
+        if form == 1:
+            r_snr, r_bh = o.simple_1d(refs[s], H, mu, sg, w=w)
+            r_path = None
+        else:
+            r_snr, r_bh, r_path = o.greedy_1d(refs[s], H, mu, sg, mitigation=mitigation, w=w)
+        # the adjoint is defined by the forward's choices: require identical ones here
+        assert np.array_equal(out.best_h.cpu().numpy()[a:b], r_bh)
+        gx_ref = o.backward_1d(form, len(x), H, r_bh, sg, gn[a:b], r_path)
+        off = int(plan.input_offsets[s])
+        got = gin[off:off + len(x)].astype(np.float64)
+        want = gx_ref * (w.astype(np.float64) if w is not None else 1.0)
+        scale = np.abs(gn[a:b]).max() / sg.min() * H
+        np.testing.assert_allclose(got, want, rtol=1e-5, atol=1e-6 * scale)
+        if w is not None:
+            gw_ref += refs[s].astype(np.float64) * gx_ref
+    if w is not None:
+        scale = np.abs(gw_ref).max()
+        np.testing.assert_allclose(gw.cpu().numpy(), gw_ref, rtol=1e-5, atol=1e-6 * scale)
+    plan.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("H", [1, 5, 16, 32])
+def test_backward_single(hs, oracle_lib, form, H):
+    x = synth.spectrum(50001, 3 + H, [synth.Pulsar(401.2, 0.05)])
+    bwd_case(hs, oracle_lib, [x], H, form)
+
+
+def test_backward_unmitigated_batch(hs, oracle_lib):
+    xs = [synth.spectrum(n, n) for n in (4099, 10000, 33, 70000)]
+    bwd_case(hs, oracle_lib, xs, 8, 2, mitigation=False)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_backward_whitening(hs, oracle_lib, dtype):
+    N = 1 << 15
+    w = synth.whitening(N, 2)
+    xs = [synth.spectrum(N, 60 + i, [synth.Pulsar(150.3 + i, 0.05)]) for i in range(4)]
+    bwd_case(hs, oracle_lib, xs, 32, 2, w=w, dtype=dtype)
+    bwd_case(hs, oracle_lib, xs, 16, 1, w=w, dtype=dtype)
+
+
+def test_autograd_topk_loss_matches_fd(hs, oracle_lib):
+    """loss = -sum of the top-16 greedy SNRs per spectrum, learnable whitening w (init 1.0):
+    the adjoint's dL/dw matches central finite differences (eps = 1e-3) of the FP64 oracle on a
+    4096-bin slice and the oracle's analytic gradient everywhere."""
+    B, N, H, K = 4, 1 << 16, 32, 16
+    pulsars = [synth.Pulsar(200.0 + 37.3 * i, 0.05) for i in range(B)]
+    ps = [synth.spectrum(N, 300 + i, [pulsars[i]]) for i in range(B)]
+    p = torch.from_numpy(np.concatenate(ps)).to(DEV)
+    w = torch.ones(N, device=DEV, requires_grad=True)
+    plan = hs.Plan(H, hs.GREEDY, lengths=[N] * B, flags=hs.FLAG_WHITENING)
+    mu, sg = hs.norm_exponential(2, 1, H)
+    nrm = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    snr, bh, path = hs.HarmonicSum.apply(p, w, plan, hs.GREEDY, *nrm)
+    nf = plan.total_fundamentals // B
+    loss = -snr.view(B, nf).topk(K, dim=1).values.sum()
+    loss.backward()
+    gw = w.grad.cpu().numpy().astype(np.float64)
+
+    o = oracle_lib
+    w0 = np.ones(N, np.float32)
+
+    def oracle_loss(wv, round_w=True):
+        tot = 0.0
+        choice = []
+        for x in ps:
+            s, b, pa = o.greedy_1d(x, H, mu, sg, w=wv, round_w=round_w)
+            top = np.argsort(-s, kind="stable")[:K]
+            tot -= s[top].sum()
+            choice.append((b, pa, top))
+        return tot, choice
+
+    L0, choice0 = oracle_loss(w0)
+    gw_ref = np.zeros(N)
+    for (b, pa, top), x in zip(choice0, ps):
+        g = np.zeros(nf)
+        g[top] = -1.0
+        gw_ref += x.astype(np.float64) * o.backward_1d(2, N, H, b, sg, g, pa)
+    np.testing.assert_allclose(gw, gw_ref, rtol=1e-5, atol=1e-6)
+    # central differences on a 4096-bin slice holding the pulsars' harmonics
+    j0 = 0                                  # bins 0..4095 hold harmonics of every pulsar
+    eps = 1e-3
+    js = list(range(j0, j0 + 4096))
+    sel = [j for j in js if gw_ref[j] != 0.0] + js[::256]
+    checked = 0
+    for j in sel:
+        wp, wm = w0.copy(), w0.copy()
+        wp[j] += eps
+        wm[j] -= eps
+        Lp, cp = oracle_loss(wp, round_w=False)
+        Lm, cm = oracle_loss(wm, round_w=False)
+        if any(not (np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]))
+               for a, b in zip(cp, cm)):
+            continue          # a discrete choice flipped inside +-eps: FD is not a derivative here
+        dw = float(np.float32(wp[j])) - float(np.float32(wm[j]))
+        fd = (Lp - Lm) / dw
+        assert abs(fd - gw[j]) <= 1e-4 * max(1.0, abs(fd)), (j, fd, gw[j])
+        checked += 1
+    assert checked >= 16
