@@ -100,13 +100,23 @@ typedef struct {
                             within the spectrum (2D: the flattened output index); ties -> lowest n */
 } hs_form_io;
 
-/* Launch shape of the 1D forward; hs_plan_create picks one (autotuned with HS_FLAG_AUTOTUNE). */
+/* Launch shape of the 1D forward; hs_plan_create picks one (autotuned with HS_FLAG_AUTOTUNE).
+ *   kernel 0: one thread per fundamental, read-only gathers of each order's bins;
+ *   kernel 1: as 0, the greedy candidates of four orders loaded at once (shorter load chain);
+ *   kernel 2: per tile of `threads` fundamentals, every order's window [h n0, h (n0+T-1) + h] is
+ *             staged in shared memory by bulk copies (TMA) through a `stages`-deep ring of
+ *             `stage_kb` KiB buffers, one producer warp + `threads` consumer threads
+ *             (not available with HS_FLAG_WHITENING). */
 typedef struct {
-    int32_t kernel;      /* 0 = direct gather, 1 = gather with greedy look-ahead */
-    int32_t threads;     /* threads per CTA: 64..1024, multiple of 32 */
-    int32_t fund_per_thread; /* 1, 2 or 4 fundamentals per thread */
-    int32_t ctas_per_sm; /* persistent grid = ctas_per_sm x SMs; 0 = one CTA per tile */
-    int32_t dynamic;     /* persistent grid takes tiles from an atomic counter (needs workspace) */
+    int32_t kernel;          /* 0, 1 or 2 */
+    int32_t threads;         /* fundamentals per CTA tile: 64..256, multiple of 32 */
+    int32_t fund_per_thread; /* 1 */
+    int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SMs; 0 = kernel 0/1: one CTA per
+                                tile, kernel 2: as many CTAs as fit on an SM */
+    int32_t dynamic;         /* kernels 0/1 with a persistent grid: tiles from an atomic counter in
+                                the workspace */
+    int32_t stages;          /* kernel 2: ring buffers, 2..4 */
+    int32_t stage_kb;        /* kernel 2: KiB per ring buffer (>= the largest order window) */
 } hs_tuning;
 
 /* Create a plan: validates `desc`, computes fundamental counts and tiles, allocates the plan's

@@ -74,7 +74,8 @@ struct hs_plan_s {
     std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
     int64_t total_fund = 0, extent = 0, max_len = 0;
     int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
-    hs_tuning tun{1, 256, 1, 0, 0};
+    hs_tuning tun{1, 256, 1, 0, 0, 0, 0};
+    WinPlan wplan{};
     // device tables
     int64_t *d_in_off = nullptr, *d_fund_off = nullptr, *d_tile_start = nullptr, *d_in_len = nullptr;
     int *d_err = nullptr;
@@ -89,6 +90,7 @@ struct hs_plan_s {
 namespace {
 
 int64_t tile_fund(const hs_tuning &t) { return static_cast<int64_t>(t.threads) * t.fund_per_thread; }
+void make_win_plan(hs_plan p);
 
 void compute_tiles(hs_plan p)
 {
@@ -96,6 +98,7 @@ void compute_tiles(hs_plan p)
     const size_t B = p->nf.size();
     p->tile_start.assign(B + 1, 0);
     for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf[s] + T - 1) / T;
+    make_win_plan(p);
 }
 
 hs_status upload_tiles(hs_plan p)
@@ -106,15 +109,74 @@ hs_status upload_tiles(hs_plan p)
     return HS_OK;
 }
 
-hs_status validate_tuning(const hs_tuning *t)
+constexpr int kMaxDynSmem = 232448 - kWinStaticSmem;   // 227 KiB opt-in per CTA, minus static
+
+hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
 {
     if (!t) return HS_ERR_INVALID_ARG;
-    if (t->kernel < 0 || t->kernel > 1) return HS_ERR_INVALID_ARG;
+    if (t->kernel < 0 || t->kernel > 2) return HS_ERR_INVALID_ARG;
     if (t->threads < 64 || t->threads > 256 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
     if (t->fund_per_thread != 1) return HS_ERR_UNSUPPORTED;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
     if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
-    if (t->dynamic && t->ctas_per_sm == 0) return HS_ERR_INVALID_ARG;
+    if (t->kernel == 2) {
+        if (p->d.flags & HS_FLAG_WHITENING) return HS_ERR_UNSUPPORTED;
+        if (t->dynamic) return HS_ERR_INVALID_ARG;
+        if (t->stages < 2 || t->stages > 4 || t->stage_kb < 1) return HS_ERR_INVALID_ARG;
+        const int64_t bb = static_cast<int64_t>(t->stage_kb) * 1024;
+        if (bb < win_bytes(p->d.H, t->threads, elem_bytes(p->d.dtype))) return HS_ERR_INVALID_ARG;
+        if (bb * t->stages > kMaxDynSmem) return HS_ERR_INVALID_ARG;
+    } else if (t->dynamic && t->ctas_per_sm == 0) {
+        return HS_ERR_INVALID_ARG;
+    }
+    return HS_OK;
+}
+
+// Pack orders 1..H into phases of at most buf_bytes each.
+void make_win_plan(hs_plan p)
+{
+    WinPlan &w = p->wplan;
+    w = WinPlan{};
+    const hs_tuning &t = p->tun;
+    if (t.kernel != 2) return;
+    w.T = t.threads;
+    w.nbuf = t.stages;
+    w.buf_bytes = t.stage_kb * 1024;
+    w.extent = p->extent;
+    int ph = 0;
+    int64_t used = 0;
+    w.phase_h0[0] = 1;
+    for (int h = 1; h <= p->d.H; ++h) {
+        const int64_t wb = win_bytes(h, t.threads, elem_bytes(p->d.dtype));
+        if (used + wb > w.buf_bytes) {
+            w.phase_h0[++ph] = h;
+            used = 0;
+        }
+        w.off[h - 1] = static_cast<int32_t>(used);
+        used += wb;
+    }
+    w.nphase = ph + 1;
+    w.phase_h0[w.nphase] = p->d.H + 1;
+}
+
+hs_tuning default_tuning(const hs_plan p)
+{
+    hs_tuning t{2, 128, 1, 0, 0, 4, 48};
+    if (validate_tuning(p, &t) == HS_OK) return t;
+    t = hs_tuning{2, 64, 1, 0, 0, 4, 48};
+    if (validate_tuning(p, &t) == HS_OK) return t;
+    return hs_tuning{1, 256, 1, 0, 0, 0, 0};
+}
+
+std::mutex g_attr_mu;
+std::vector<const void *> g_attr_set;
+
+hs_status ensure_dyn_smem(const void *fn)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (std::find(g_attr_set.begin(), g_attr_set.end(), fn) != g_attr_set.end()) return HS_OK;
+    HS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+    g_attr_set.push_back(fn);
     return HS_OK;
 }
 
@@ -215,6 +277,24 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.s = to_form_args(simple);
     a.g = to_form_args(greedy);
     a.err = p->d_err;
+    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    if (t.kernel == 2) {
+        const size_t smem = static_cast<size_t>(p->wplan.nbuf) * p->wplan.buf_bytes;
+        hs_status es = ensure_dyn_smem(fn);
+        if (es != HS_OK) return es;
+        int per_sm = t.ctas_per_sm;
+        if (per_sm == 0) {
+            HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, t.threads + 32, smem));
+            if (per_sm < 1) return HS_ERR_UNSUPPORTED;
+        }
+        int64_t grid = std::min<int64_t>(a.total_tiles, static_cast<int64_t>(per_sm) * p->sms);
+        if (grid < 1) return HS_OK;
+        WinPlan wp = p->wplan;
+        void *args[] = {&a, &wp};
+        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads + 32), args, smem, st));
+        return HS_OK;
+    }
     int64_t grid = a.total_tiles;
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
     if (t.dynamic) {
@@ -224,8 +304,6 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     }
     if (grid < 1) return HS_OK;
     if (grid > 0x7fffffff) return HS_ERR_UNSUPPORTED;
-    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
-    if (!fn) return HS_ERR_UNSUPPORTED;
     void *args[] = {&a};
     HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
     return HS_OK;
@@ -330,10 +408,16 @@ hs_status autotune(hs_plan p)
         fg.path = nullptr;
         if (!cuda_ok(cudaStreamSynchronize(s))) { result = HS_ERR_CUDA; goto done; }
     }
+    for (int threads : {64, 128, 256})
+        for (int stages : {2, 3, 4})
+            for (int kb : {24, 32, 48, 64, 96}) {
+                hs_tuning t{2, threads, 1, 0, 0, stages, kb};
+                if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
+            }
     for (int kernel = 0; kernel <= 1; ++kernel)
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
-                hs_tuning t{kernel, threads, 1, 0, 0};
+                hs_tuning t{kernel, threads, 1, 0, 0, 0, 0};
                 if (sched >= 1) {
                     int occ = 0;
                     const void *fn = fwd1d_kernel(sd.dtype, sd.forms, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
@@ -538,6 +622,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         delete p;
         return HS_ERR_INVALID_ARG;
     }
+    if (d.dims == 1) p->tun = default_tuning(p);
     compute_tiles(p);
     if (p->no_device) {
         *out = p;
@@ -621,9 +706,9 @@ hs_status hs_plan_get_tuning(hs_plan p, hs_tuning *t)
 hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
 {
     if (!p) return HS_ERR_INVALID_ARG;
-    hs_status st = validate_tuning(t);
-    if (st != HS_OK) return st;
     if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
+    hs_status st = validate_tuning(p, t);
+    if (st != HS_OK) return st;
     std::lock_guard<std::mutex> lk(p->mu);
     p->tun = *t;
     compute_tiles(p);

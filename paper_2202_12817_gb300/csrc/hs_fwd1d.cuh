@@ -304,8 +304,12 @@ static const void *fwd1d_kernel_ptr(int kernel)
 }
 
 template <typename T>
+static const void *fwd1d_win_kernel_for(int forms);
+
+template <typename T>
 static const void *fwd1d_kernel_for(int forms, int whitening, int kernel)
 {
+    if (kernel == 2) return whitening ? nullptr : fwd1d_win_kernel_for<T>(forms);
     if (whitening) {
         switch (forms) {
         case 1: return fwd1d_kernel_ptr<T, 1, true>(kernel);

@@ -1,5 +1,6 @@
 // 1D forward kernels instantiated for stored type __half.
 #include "hs_fwd1d.cuh"
+#include "hs_fwd1d_win.cuh"
 
 namespace hs {
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel)

@@ -1,5 +1,6 @@
 // 1D forward kernels instantiated for stored type float.
 #include "hs_fwd1d.cuh"
+#include "hs_fwd1d_win.cuh"
 
 namespace hs {
 const void *fwd1d_kernel_f32(int forms, int whitening, int kernel)

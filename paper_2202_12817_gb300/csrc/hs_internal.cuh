@@ -50,6 +50,29 @@ struct Fwd1DArgs {
     int *err;                      // device error word
 };
 
+// Shared-memory staging plan of the window kernel (kernel 2): the orders 1..H of a tile are
+// packed into phases, each phase's windows filling one of `nbuf` ring buffers.
+struct WinPlan {
+    int32_t T;                        // fundamentals per tile (= consumer threads)
+    int32_t nphase;                   // phases per tile
+    int32_t nbuf;                     // ring buffers (2..4)
+    int32_t buf_bytes;                // bytes per ring buffer
+    int64_t extent;                   // readable elements of the input buffer
+    int32_t phase_h0[kMaxH1D + 1];    // phase p covers orders [phase_h0[p], phase_h0[p+1])
+    int32_t off[kMaxH1D];             // byte offset of order h's window (index h-1) in its buffer
+};
+
+// Bytes of the order-h window of a T-fundamental tile: h (T-1) + h + 1 elements plus up to
+// one 16-byte alignment unit at each end, rounded to 16 bytes.
+inline int64_t win_bytes(int h, int T, int elem)
+{
+    const int64_t a = 16 / elem;
+    const int64_t n = static_cast<int64_t>(h) * (T - 1) + h + 1 + 2 * (a - 1);
+    return (n * elem + 15) / 16 * 16;
+}
+
+constexpr int kWinStaticSmem = 2048;  // static shared memory of the window kernel (upper bound)
+
 // 2D forward launch arguments.
 struct Fwd2DArgs {
     const float *plane;
@@ -90,7 +113,8 @@ struct Bwd1DArgs {
 };
 
 // ---- kernel entry points (defined in the kernel translation units) ----
-// 1D forward: kernel 0 = direct gather, 1 = greedy look-ahead; forms 1..3; whitening 0/1.
+// 1D forward: kernel 0 = direct gather, 1 = greedy look-ahead gather, 2 = shared-memory
+// windows staged by bulk copies (launched with a WinPlan as second parameter).
 const void *fwd1d_kernel_f32(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);

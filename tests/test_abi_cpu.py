@@ -132,12 +132,27 @@ def test_tuning_validation(hs):
     p = plan(hs, H=8, forms=3, lengths=[10000])
     t = p.tuning
     assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
+    assert t.kernel == 2 and t.stages >= 2
     p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
-    assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
+    assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1,
+                                      stages=0, stage_kb=0)
+    p.tuning = dict(kernel=2, threads=256, stages=2, stage_kb=96)
+    big = plan(hs, H=32, forms=3, lengths=[100000])
+    with pytest.raises(hs.HSError):      # order-32 window of a 256-wide tile needs ~32 KiB
+        big.tuning = dict(kernel=2, threads=256, stages=4, stage_kb=24)
+    with pytest.raises(hs.HSError):      # more than 227 KiB of shared memory
+        big.tuning = dict(kernel=2, threads=128, stages=4, stage_kb=64)
+    white = plan(hs, H=8, forms=3, lengths=[1000, 1000], flags=hs.FLAG_WHITENING)
+    assert white.tuning.kernel == 1
+    with pytest.raises(hs.HSError) as e:
+        white.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=16)
+    assert e.value.status == 2
     for bad in (dict(kernel=2, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
                 dict(kernel=0, threads=100, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
                 dict(kernel=0, threads=512, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
-                dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=1)):
+                dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=1),
+                dict(kernel=2, threads=128, stages=1, stage_kb=48),
+                dict(kernel=2, threads=128, stages=5, stage_kb=8)):
         with pytest.raises(hs.HSError):
             p.tuning = bad
 

@@ -82,11 +82,15 @@ def run_case(hs, o, spectra, H, forms=3, dtype=0, mitigation=True, w=None, tunin
     return near
 
 
-TUNINGS = [dict(kernel=0, threads=256, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
-           dict(kernel=1, threads=256, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
-           dict(kernel=1, threads=128, fund_per_thread=1, ctas_per_sm=2, dynamic=0),
-           dict(kernel=0, threads=64, fund_per_thread=1, ctas_per_sm=1, dynamic=1),
-           dict(kernel=1, threads=192, fund_per_thread=1, ctas_per_sm=3, dynamic=1)]
+TUNINGS = [dict(kernel=0, threads=256),
+           dict(kernel=1, threads=256),
+           dict(kernel=1, threads=128, ctas_per_sm=2),
+           dict(kernel=0, threads=64, ctas_per_sm=1, dynamic=1),
+           dict(kernel=1, threads=192, ctas_per_sm=3, dynamic=1),
+           dict(kernel=2, threads=128, stages=4, stage_kb=48),
+           dict(kernel=2, threads=64, stages=2, stage_kb=16, ctas_per_sm=3),
+           dict(kernel=2, threads=256, stages=2, stage_kb=96, ctas_per_sm=1),
+           dict(kernel=2, threads=96, stages=3, stage_kb=20, ctas_per_sm=2)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -96,12 +100,25 @@ def test_fused_f32_shapes(hs, oracle_lib, H, tuning):
     run_case(hs, oracle_lib, [x], H, tuning=tuning)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("forms", [1, 2, 3])
 @pytest.mark.parametrize("mitigation", [True, False])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
-def test_forms_dtypes(hs, oracle_lib, forms, mitigation, dtype):
+def test_forms_dtypes(hs, oracle_lib, forms, mitigation, dtype, kernel):
     x = synth.single_pulse_spectrum()
-    run_case(hs, oracle_lib, [x], 32, forms=forms, dtype=dtype, mitigation=mitigation)
+    t = TUNINGS[5] if kernel == 2 else TUNINGS[1]
+    run_case(hs, oracle_lib, [x], 32, forms=forms, dtype=dtype, mitigation=mitigation, tuning=t)
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("n", [4097, 4098, 4099, 40003])
+def test_window_unaligned_tails(hs, oracle_lib, dtype, n):
+    """Spectra whose last window ends off a 16-byte boundary at the very end of the input
+    buffer: the bulk copy stops at the last whole 16-byte unit and the rest is loaded directly."""
+    xs = [synth.spectrum(n - 7, 3), synth.spectrum(n, 4)]
+    for t in (TUNINGS[5], TUNINGS[6]):
+        run_case(hs, oracle_lib, xs, 7, dtype=dtype, tuning=t)
+        run_case(hs, oracle_lib, xs, 32, dtype=dtype, tuning=t)
 
 
 @pytest.mark.parametrize("kernel", [0, 1])
@@ -111,7 +128,7 @@ def test_whitening(hs, oracle_lib, kernel):
     xs = [synth.spectrum(N, 50 + i, [synth.Pulsar(300.4 + 17 * i, 0.07)]) for i in range(3)]
     for dtype in (0, 1, 2):
         run_case(hs, oracle_lib, xs, 16, w=w, dtype=dtype,
-                 tuning=dict(kernel=kernel, threads=256, fund_per_thread=1, ctas_per_sm=0, dynamic=0))
+                 tuning=dict(kernel=kernel, threads=256))
 
 
 def test_small_and_degenerate_lengths(hs, oracle_lib):
@@ -126,7 +143,7 @@ def test_small_and_degenerate_lengths(hs, oracle_lib):
 def test_uneven_batch_per_spectrum_norm(hs, oracle_lib):
     b = synth.uneven_batch(count=24, seed=77, choices=(1 << 12, 1 << 13, 1 << 15, 1 << 17), pulsar_fraction=0.25)
     xs = [synth.batch_trial(b, i) for i in range(24)]
-    for t in (TUNINGS[1], TUNINGS[4]):
+    for t in (TUNINGS[1], TUNINGS[4], TUNINGS[5], TUNINGS[8]):
         run_case(hs, oracle_lib, xs, 16, per_spec_norm=True, tuning=t)
         run_case(hs, oracle_lib, xs, 16, dtype=1, tuning=t)
 
