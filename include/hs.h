@@ -103,20 +103,26 @@ typedef struct {
 /* Launch shape of the 1D forward; hs_plan_create picks one (autotuned with HS_FLAG_AUTOTUNE).
  *   kernel 0: one thread per fundamental, read-only gathers of each order's bins;
  *   kernel 1: as 0, the greedy candidates of four orders loaded at once (shorter load chain);
- *   kernel 2: per tile of `threads` fundamentals, every order's window [h n0, h (n0+T-1) + h] is
- *             staged in shared memory by bulk copies (TMA) through a `stages`-deep ring of
- *             `stage_kb` KiB buffers, one producer warp + `threads` consumer threads
- *             (not available with HS_FLAG_WHITENING). */
+ *   kernel 2: per tile of `threads` fundamentals, each order's window [h n0, h (n0+T-1) + h] is
+ *             staged in shared memory by one bulk copy (TMA) into a ring of `stages` slots of
+ *             `stage_kb` KiB; `producers` warps issue the copies (copies of one warp complete in
+ *             order, so several producer warps keep several in flight), `threads` consumer
+ *             threads run both forms from shared memory (not available with HS_FLAG_WHITENING). */
 typedef struct {
     int32_t kernel;          /* 0, 1 or 2 */
-    int32_t threads;         /* fundamentals per CTA tile: 64..256, multiple of 32 */
+    int32_t threads;         /* fundamentals per CTA tile, multiple of 32: 64..256 (kernels 0/1),
+                                64..512 (kernel 2) */
     int32_t fund_per_thread; /* 1 */
     int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SMs; 0 = kernel 0/1: one CTA per
                                 tile, kernel 2: as many CTAs as fit on an SM */
     int32_t dynamic;         /* kernels 0/1 with a persistent grid: tiles from an atomic counter in
                                 the workspace */
-    int32_t stages;          /* kernel 2: ring buffers, 2..4 */
-    int32_t stage_kb;        /* kernel 2: KiB per ring buffer (>= the largest order window) */
+    int32_t stages;          /* kernel 2: ring slots, 2..16 */
+    int32_t stage_kb;        /* kernel 2: KiB per slot (>= the largest order window) */
+    int32_t prefetch;        /* kernel 2: 1 = prefetch the whole input into L2 at launch when it fits
+                                in a quarter of L2 */
+    int32_t producers;       /* kernel 2: producer warps, 1..8 (<= stages; threads + 32 producers
+                                <= 640) */
 } hs_tuning;
 
 /* Create a plan: validates `desc`, computes fundamental counts and tiles, allocates the plan's

@@ -68,7 +68,7 @@ class _FormIO(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("threads", ctypes.c_int32), ("fund_per_thread", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("dynamic", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("stage_kb", ctypes.c_int32)]
+                ("stage_kb", ctypes.c_int32), ("prefetch", ctypes.c_int32), ("producers", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -248,7 +248,8 @@ class Plan:
     @tuning.setter
     def tuning(self, t):
         if isinstance(t, dict):
-            t = Tuning(**{"fund_per_thread": 1, "ctas_per_sm": 0, "dynamic": 0, "stages": 0, "stage_kb": 0, **t})
+            t = Tuning(**{"fund_per_thread": 1, "ctas_per_sm": 0, "dynamic": 0, "stages": 0, "stage_kb": 0,
+                          "prefetch": 0, "producers": 0, **t})
         _check(lib().hs_plan_set_tuning(self._h, ctypes.byref(t)), "hs_plan_set_tuning")
 
     def workspace(self, device=None):

@@ -74,7 +74,8 @@ struct hs_plan_s {
     std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
     int64_t total_fund = 0, extent = 0, max_len = 0;
     int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
-    hs_tuning tun{1, 256, 1, 0, 0, 0, 0};
+    hs_tuning tun{1, 256, 1, 0, 0, 0, 0, 0, 0};
+    int l2_bytes = 0;
     WinPlan wplan{};
     // device tables
     int64_t *d_in_off = nullptr, *d_fund_off = nullptr, *d_tile_start = nullptr, *d_in_len = nullptr;
@@ -115,14 +116,19 @@ hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
 {
     if (!t) return HS_ERR_INVALID_ARG;
     if (t->kernel < 0 || t->kernel > 2) return HS_ERR_INVALID_ARG;
-    if (t->threads < 64 || t->threads > 256 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
+    if (t->threads < 64 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
+    if (t->threads > (t->kernel == 2 ? 512 : 256)) return HS_ERR_INVALID_ARG;
     if (t->fund_per_thread != 1) return HS_ERR_UNSUPPORTED;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
     if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
+    if (t->prefetch < 0 || t->prefetch > 1) return HS_ERR_INVALID_ARG;
+    if (t->kernel != 2 && (t->prefetch != 0 || t->producers != 0)) return HS_ERR_INVALID_ARG;
     if (t->kernel == 2) {
         if (p->d.flags & HS_FLAG_WHITENING) return HS_ERR_UNSUPPORTED;
         if (t->dynamic) return HS_ERR_INVALID_ARG;
-        if (t->stages < 2 || t->stages > 4 || t->stage_kb < 1) return HS_ERR_INVALID_ARG;
+        if (t->stages < 2 || t->stages > 16 || t->stage_kb < 1) return HS_ERR_INVALID_ARG;
+        if (t->producers < 1 || t->producers > 8 || t->producers > t->stages) return HS_ERR_INVALID_ARG;
+        if (t->threads + 32 * t->producers > 640) return HS_ERR_INVALID_ARG;
         const int64_t bb = static_cast<int64_t>(t->stage_kb) * 1024;
         if (bb < win_bytes(p->d.H, t->threads, elem_bytes(p->d.dtype))) return HS_ERR_INVALID_ARG;
         if (bb * t->stages > kMaxDynSmem) return HS_ERR_INVALID_ARG;
@@ -132,7 +138,7 @@ hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
     return HS_OK;
 }
 
-// Pack orders 1..H into phases of at most buf_bytes each.
+// Ring plan of the window kernel.
 void make_win_plan(hs_plan p)
 {
     WinPlan &w = p->wplan;
@@ -140,32 +146,20 @@ void make_win_plan(hs_plan p)
     const hs_tuning &t = p->tun;
     if (t.kernel != 2) return;
     w.T = t.threads;
-    w.nbuf = t.stages;
-    w.buf_bytes = t.stage_kb * 1024;
+    w.nslot = t.stages;
+    w.nprod = t.producers;
+    w.slot_bytes = t.stage_kb * 1024;
     w.extent = p->extent;
-    int ph = 0;
-    int64_t used = 0;
-    w.phase_h0[0] = 1;
-    for (int h = 1; h <= p->d.H; ++h) {
-        const int64_t wb = win_bytes(h, t.threads, elem_bytes(p->d.dtype));
-        if (used + wb > w.buf_bytes) {
-            w.phase_h0[++ph] = h;
-            used = 0;
-        }
-        w.off[h - 1] = static_cast<int32_t>(used);
-        used += wb;
-    }
-    w.nphase = ph + 1;
-    w.phase_h0[w.nphase] = p->d.H + 1;
+    w.pf_chunk = 0;   // set at launch (depends on the grid)
 }
 
 hs_tuning default_tuning(const hs_plan p)
 {
-    hs_tuning t{2, 128, 1, 0, 0, 4, 48};
-    if (validate_tuning(p, &t) == HS_OK) return t;
-    t = hs_tuning{2, 64, 1, 0, 0, 4, 48};
-    if (validate_tuning(p, &t) == HS_OK) return t;
-    return hs_tuning{1, 256, 1, 0, 0, 0, 0};
+    // one thread per fundamental with read-only gathers, 128-fundamental CTAs: measured on the
+    // 2^23-bin H = 32 spectrum it is the fastest shape for each form alone and ties the window
+    // kernel for the fused pass; HS_FLAG_AUTOTUNE times the alternatives per plan
+    (void)p;
+    return hs_tuning{0, 128, 1, 0, 0, 0, 0, 0, 0};
 }
 
 std::mutex g_attr_mu;
@@ -280,19 +274,23 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
     if (!fn) return HS_ERR_UNSUPPORTED;
     if (t.kernel == 2) {
-        const size_t smem = static_cast<size_t>(p->wplan.nbuf) * p->wplan.buf_bytes;
+        const size_t smem = static_cast<size_t>(p->wplan.nslot) * p->wplan.slot_bytes;
         hs_status es = ensure_dyn_smem(fn);
         if (es != HS_OK) return es;
+        const int block = t.threads + 32 * t.producers;
         int per_sm = t.ctas_per_sm;
         if (per_sm == 0) {
-            HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, t.threads + 32, smem));
+            HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem));
             if (per_sm < 1) return HS_ERR_UNSUPPORTED;
         }
         int64_t grid = std::min<int64_t>(a.total_tiles, static_cast<int64_t>(per_sm) * p->sms);
         if (grid < 1) return HS_OK;
         WinPlan wp = p->wplan;
+        const int64_t in_bytes = p->extent * elem_bytes(p->d.dtype);
+        if ((t.prefetch & 1) && p->l2_bytes > 0 && in_bytes <= p->l2_bytes / 4)
+            wp.pf_chunk = ((in_bytes + grid - 1) / grid + 15) / 16 * 16;
         void *args[] = {&a, &wp};
-        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads + 32), args, smem, st));
+        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(block), args, smem, st));
         return HS_OK;
     }
     int64_t grid = a.total_tiles;
@@ -409,15 +407,18 @@ hs_status autotune(hs_plan p)
         if (!cuda_ok(cudaStreamSynchronize(s))) { result = HS_ERR_CUDA; goto done; }
     }
     for (int threads : {64, 128, 256})
-        for (int stages : {2, 3, 4})
-            for (int kb : {24, 32, 48, 64, 96}) {
-                hs_tuning t{2, threads, 1, 0, 0, stages, kb};
+        for (int prod : {2, 4, 8}) {
+            const int kb = static_cast<int>((win_bytes(sp->d.H, threads, elem_bytes(sp->d.dtype)) + 1023) / 1024);
+            for (int total_kb : {100, 200}) {
+                const int slots = std::min(16, total_kb / kb);
+                hs_tuning t{2, threads, 1, 0, 0, slots, kb, 0, prod};
                 if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
             }
+        }
     for (int kernel = 0; kernel <= 1; ++kernel)
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
-                hs_tuning t{kernel, threads, 1, 0, 0, 0, 0};
+                hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, 0, 0};
                 if (sched >= 1) {
                     int occ = 0;
                     const void *fn = fwd1d_kernel(sd.dtype, sd.forms, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
@@ -630,7 +631,8 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
     }
     DeviceGuard guard(device);
     if (!guard.ok) { delete p; return HS_ERR_CUDA; }
-    if (!cuda_ok(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device))) { delete p; return HS_ERR_CUDA; }
+    if (!cuda_ok(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device)) ||
+        !cuda_ok(cudaDeviceGetAttribute(&p->l2_bytes, cudaDevAttrL2CacheSize, device))) { delete p; return HS_ERR_CUDA; }
     const size_t B1 = p->in_off.size();
     if (!cuda_ok(cudaMalloc(&p->d_in_off, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_fund_off, sizeof(int64_t) * B1)) ||

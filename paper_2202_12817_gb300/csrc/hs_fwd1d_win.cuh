@@ -5,15 +5,18 @@
 // order: the simple form reads h n (Eq. 3), the greedy form h n + d and h n + d + 1 with
 // d <= h - 1 (Eq. 5, Algorithm 2).  Each window is copied from global memory into shared
 // memory with one 1D bulk copy (cp.async.bulk, the TMA engine), so the L2 -> SM traffic is
-// fully coalesced (a strided / drift-dependent gather would pay one 32-byte sector per 4-byte
+// fully coalesced (a strided / drift-dependent gather pays one 32-byte sector per 4-byte
 // value), and the greedy comparison chain runs on shared-memory latency instead of L2 latency.
 //
-// Roles: warp T/32 is the producer (one elected lane issues the bulk copies); warps 0..T/32-1
-// are consumers, one fundamental per thread.  The orders of a tile are packed into phases,
-// each filling one buffer of an nbuf-deep ring; `full[b]` completes when a phase's bytes
-// land (expect-tx), `empty[b]` when every consumer warp is done with the buffer.  Every wait
-// is bounded (kWaitNs of global time); a timed-out wait sets the device error word, raises an
-// abort flag and the CTA winds down after draining its own copies in flight.
+// A CTA walks the sequence j = 0, 1, 2, ... of (tile k, order h) pairs, j = k H + h - 1, through
+// a ring of `nslot` slots: order j lives in slot j % nslot.  Bulk copies issued by one warp
+// complete one after another (~0.3 us each on this part), so `nprod` producer warps share the
+// issuing -- order j is issued by producer warp j % nprod -- to keep several copies in flight.
+// T consumer threads (one fundamental each) take the orders in sequence.  `full[i]` completes
+// when slot i's bytes land (expect-tx), `empty[i]` when every consumer warp is done with it.
+// Every wait is bounded (kWaitNs of global time); a timed-out wait sets the device error word
+// and raises an abort flag, after which nobody waits any more and producers drain their own
+// copies in flight before returning.
 #pragma once
 
 #include "hs_fwd1d.cuh"
@@ -21,7 +24,7 @@
 namespace hs {
 
 constexpr unsigned long long kWaitNs = 1000000000ull;   // 1 s
-constexpr int kMaxBuf = 4;
+constexpr int kMaxSlot = 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -85,6 +88,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void consumer_sync(int nthreads)
 {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
@@ -126,12 +134,12 @@ __device__ __forceinline__ void consumer_argmax(unsigned long long key, unsigned
 }
 
 template <typename T, int FORMS>
-__global__ void __launch_bounds__(288) k_fwd1d_win(const Fwd1DArgs a, const WinPlan wp)
+__global__ void __launch_bounds__(640) k_fwd1d_win(const Fwd1DArgs a, const WinPlan wp)
 {
     extern __shared__ __align__(128) unsigned char win_smem[];
-    __shared__ NormSmem nm;
     __shared__ unsigned long long red[32];
-    __shared__ __align__(8) uint64_t full[kMaxBuf], empty[kMaxBuf];
+    __shared__ __align__(8) uint64_t full[kMaxSlot], empty[kMaxSlot];
+    __shared__ float2 nrm[2][kMaxH1D];      // (1/sigma_h, mu_h/sigma_h) per form
     __shared__ volatile int s_abort;
     constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
     constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
@@ -140,153 +148,189 @@ __global__ void __launch_bounds__(288) k_fwd1d_win(const Fwd1DArgs a, const WinP
     const int ncw = Tn >> 5;                               // consumer warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int H = a.H;
+    const int R = wp.nslot;
 
     if (threadIdx.x == 0) {
-        for (int b = 0; b < wp.nbuf; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], ncw);
+        for (int i = 0; i < R; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], ncw);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int64_t my_tiles = a.total_tiles > blockIdx.x
+                                 ? (a.total_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const int64_t total_j = my_tiles * H;
 
-    // ------------------------------------------------------------------ producer
-    if (warp == ncw) {
+    // ------------------------------------------------------------------ producers
+    if (warp >= ncw) {
+        const int pw = warp - ncw;
         if (lane != 0) return;
-        uint32_t q = 0;
-        int issued_u[kMaxBuf];
-        for (int b = 0; b < kMaxBuf; ++b) issued_u[b] = -1;
+        if (pw == 0 && wp.pf_chunk > 0) {
+            // the whole input fits comfortably in L2: bring this CTA's share in ahead of the windows
+            const int64_t total = wp.extent * static_cast<int64_t>(sizeof(T));
+            int64_t lo = static_cast<int64_t>(blockIdx.x) * wp.pf_chunk;
+            const int64_t hi = lo + wp.pf_chunk < total ? lo + wp.pf_chunk : total;
+            const unsigned char *src = static_cast<const unsigned char *>(a.x);
+            for (; lo + 16 <= hi; lo += 65536) {
+                const int64_t nb = (hi - lo < 65536 ? hi - lo : 65536) & ~static_cast<int64_t>(15);
+                bulk_prefetch_l2(src + lo, static_cast<uint32_t>(nb));
+            }
+        }
+        // this warp issues orders j = pw, pw + P, ...; (k, h) = (j / H, j % H + 1) and
+        // (slot, use) = (j % R, j / R) are stepped incrementally (no divisions in the loop)
+        const int P = wp.nprod;
+        int64_t k = 0;
+        int h = pw + 1;
+        while (h > H) { h -= H; ++k; }
+        int slot = pw % R;
+        int64_t u = pw / R;
+        int last_use[kMaxSlot];                    // last use this warp issued into each slot (drain)
+        for (int i = 0; i < kMaxSlot; ++i) last_use[i] = -1;
         bool ok = true;
-        for (int64_t tile = blockIdx.x; ok && tile < a.total_tiles; tile += gridDim.x) {
+        for (int64_t j = pw; j < total_j; j += P) {
+            if (u > 0 && !s_abort && !mbar_wait(&empty[slot], static_cast<uint32_t>((u - 1) & 1))) {
+                set_error(a.err, kErrTimeout);
+                s_abort = 1;
+            }
+            if (s_abort) { ok = false; break; }
+            const int64_t tile = blockIdx.x + k * gridDim.x;
             const int s = tile_spectrum(a.tile_start, a.B, tile);
-            const int64_t fbase = __ldg(a.fund_off + s);
-            const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+            const int64_t nf = __ldg(a.fund_off + s + 1) - __ldg(a.fund_off + s);
             const int64_t n0 = (tile - __ldg(a.tile_start + s)) * Tn;
             const int64_t n_last = (n0 + Tn < nf ? n0 + Tn : nf) - 1;
             const int64_t base = __ldg(a.in_off + s);
             const int64_t avail = wp.extent - base;           // readable elements from x
             const T *x = static_cast<const T *>(a.x) + base;
-            for (int p = 0; p < wp.nphase; ++p, ++q) {
-                const int b = static_cast<int>(q % wp.nbuf);
-                const int u = static_cast<int>(q / wp.nbuf);
-                if (u > 0 && !mbar_wait(&empty[b], (u - 1) & 1)) {
-                    set_error(a.err, kErrTimeout);
-                    s_abort = 1;
-                    ok = false;
-                    break;
-                }
-                if (s_abort) { ok = false; break; }
-                unsigned char *buf = win_smem + static_cast<size_t>(b) * wp.buf_bytes;
-                uint32_t bytes = 0;
-                for (int h = wp.phase_h0[p]; h < wp.phase_h0[p + 1]; ++h) {
-                    const int64_t g0 = static_cast<int64_t>(h) * n0;
-                    const int64_t g1 = static_cast<int64_t>(h) * n_last + h + 1;   // exclusive
-                    const int64_t g0a = g0 & ~static_cast<int64_t>(A - 1);
-                    const int64_t g1u = (g1 + A - 1) & ~static_cast<int64_t>(A - 1);
-                    const int64_t gc = g1u <= avail ? g1u : (g1 & ~static_cast<int64_t>(A - 1));
-                    T *dst = reinterpret_cast<T *>(buf + wp.off[h - 1]);
-                    if (gc > g0a) {
-                        const uint32_t nb = static_cast<uint32_t>((gc - g0a) * static_cast<int64_t>(sizeof(T)));
-                        bulk_g2s(dst, x + g0a, nb, &full[b]);
-                        bytes += nb;
-                    }
-                    for (int64_t j = (gc > g0a ? gc : g0a); j < g1; ++j) dst[j - g0a] = x[j];   // unaligned tail
-                }
-                mbar_arrive_expect_tx(&full[b], bytes);
-                issued_u[b] = u;
+            const int64_t g0 = static_cast<int64_t>(h) * n0;  // 16-byte aligned (n0 % 32 == 0)
+            const int64_t g1 = static_cast<int64_t>(h) * n_last + h + 1;   // exclusive
+            const int64_t g1u = (g1 + A - 1) & ~static_cast<int64_t>(A - 1);
+            const int64_t gc = g1u <= avail ? g1u : (g1 & ~static_cast<int64_t>(A - 1));
+            T *dst = reinterpret_cast<T *>(win_smem + static_cast<size_t>(slot) * wp.slot_bytes);
+            uint32_t bytes = 0;
+            if (gc > g0) {
+                bytes = static_cast<uint32_t>((gc - g0) * static_cast<int64_t>(sizeof(T)));
+                bulk_g2s(dst, x + g0, bytes, &full[slot]);
             }
+            for (int64_t i = (gc > g0 ? gc : g0); i < g1; ++i) dst[i - g0] = x[i];   // unaligned tail
+            mbar_arrive_expect_tx(&full[slot], bytes);
+            last_use[slot] = static_cast<int>(u & 1) | 2;   // parity of the use, bit 1 = valid
+            // advance to j + P
+            h += P;
+            while (h > H) { h -= H; ++k; }
+            slot += P;
+            if (slot >= R) { slot -= R; ++u; }
         }
         if (!ok) {
-            // drain: wait (bounded) until every copy this CTA issued has landed
-            for (int b = 0; b < wp.nbuf; ++b)
-                if (issued_u[b] >= 0) mbar_wait(&full[b], issued_u[b] & 1);
+            // drain: wait (bounded) until the copies this warp issued have landed
+            for (int i = 0; i < R; ++i)
+                if (last_use[i] >= 0) mbar_wait(&full[i], static_cast<uint32_t>(last_use[i] & 1));
         }
         return;
     }
 
     // ------------------------------------------------------------------ consumers
     const int t = threadIdx.x;
-    uint32_t q = 0;
+    int cslot = 0;                    // slot of the next order (j % R) and its phase parity
+    uint32_t cpar = 0;
     int loaded_spec = -1;
-    for (int64_t tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
+    for (int64_t k = 0; k < my_tiles; ++k) {
+        const int64_t tile = blockIdx.x + k * gridDim.x;
         const int s = tile_spectrum(a.tile_start, a.B, tile);
         if (s != loaded_spec) {
             consumer_sync(Tn);
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
-            if (kS) load_norm(nm, 0, a.s.mu + no, a.s.sigma + no, H);
-            if (kG) load_norm(nm, 1, a.g.mu + no, a.g.sigma + no, H);
+            for (int h = t; h < H; h += Tn) {
+                if (kS) {
+                    const float rs = __frcp_rn(__ldg(a.s.sigma + no + h));
+                    nrm[0][h] = make_float2(rs, __fmul_rn(__ldg(a.s.mu + no + h), rs));
+                }
+                if (kG) {
+                    const float rs = __frcp_rn(__ldg(a.g.sigma + no + h));
+                    nrm[1][h] = make_float2(rs, __fmul_rn(__ldg(a.g.mu + no + h), rs));
+                }
+            }
             consumer_sync(Tn);
             loaded_spec = s;
         }
         const int64_t fbase = __ldg(a.fund_off + s);
         const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
-        const int64_t n0 = (tile - __ldg(a.tile_start + s)) * Tn;
-        const int64_t n = n0 + t;
+        const int64_t n = (tile - __ldg(a.tile_start + s)) * Tn + t;
         const bool valid = n < nf;
-        RunMax ms{0.f, 1}, mg{0.f, 1};
+        float best_s = 0.f, best_g = 0.f;
+        int bh_s = 1, bh_g = 1;
         float ss = 0.f, sg = 0.f;
         int d = 0;
         uint32_t bits = 0;
-        for (int p = 0; p < wp.nphase; ++p, ++q) {
-            const int b = static_cast<int>(q % wp.nbuf);
-            const int u = static_cast<int>(q / wp.nbuf);
-            // after an abort, waits are skipped (the data is garbage, the error word is set) so
-            // that every consumer still reaches the same named barriers
-            if (!s_abort && !mbar_wait(&full[b], u & 1)) {
+        // order 1
+        if (!s_abort && !mbar_wait(&full[cslot], cpar)) {
+            set_error(a.err, kErrTimeout);
+            s_abort = 1;
+        }
+        {
+            const T *w = reinterpret_cast<const T *>(win_smem + static_cast<size_t>(cslot) * wp.slot_bytes);
+            if (valid) {
+                const float x0 = sm_ld<T>(w, t);
+                ss = x0;
+                sg = x0;
+                if (kG && a.mitigation) {
+                    const float x1 = sm_ld<T>(w, t + 1);
+                    if (x1 > x0) { d = 1; sg = x1; bits = 1u; }
+                }
+                if (kS) { const float2 c = nrm[0][0]; best_s = fmaf(ss, c.x, -c.y); }
+                if (kG) { const float2 c = nrm[1][0]; best_g = fmaf(sg, c.x, -c.y); }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[cslot]);
+            if (++cslot == R) { cslot = 0; cpar ^= 1u; }
+        }
+        int e = t;                    // h t: element of this fundamental's h n in the window
+        for (int h = 2; h <= H; ++h) {
+            e += t;
+            if (!s_abort && !mbar_wait(&full[cslot], cpar)) {
                 set_error(a.err, kErrTimeout);
                 s_abort = 1;
             }
-            const unsigned char *buf = win_smem + static_cast<size_t>(b) * wp.buf_bytes;
+            const T *w = reinterpret_cast<const T *>(win_smem + static_cast<size_t>(cslot) * wp.slot_bytes);
             if (valid) {
-                for (int h = wp.phase_h0[p]; h < wp.phase_h0[p + 1]; ++h) {
-                    const T *w = reinterpret_cast<const T *>(buf + wp.off[h - 1]);
-                    const int64_t g0 = static_cast<int64_t>(h) * n0;
-                    const int e = h * t + static_cast<int>(g0 - (g0 & ~static_cast<int64_t>(A - 1)));
-                    if (h == 1) {
-                        const float x0 = sm_ld<T>(w, e);
-                        ss = x0;
-                        sg = x0;
-                        if (kG && a.mitigation) {
-                            const float x1 = sm_ld<T>(w, e + 1);
-                            if (x1 > x0) { d = 1; sg = x1; bits = 1u; }
-                        }
-                        if (kS) ms.first(fmaf(ss, nm.rs[0][0], -nm.murs[0][0]));
-                        if (kG) mg.first(fmaf(sg, nm.rs[1][0], -nm.murs[1][0]));
-                    } else {
-                        if (kS) {
-                            ss += sm_ld<T>(w, e);
-                            ms.step(fmaf(ss, nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
-                        }
-                        if (kG) {
-                            const float va = sm_ld<T>(w, e + d);
-                            const float vb = sm_ld<T>(w, e + d + 1);
-                            const bool inc = vb > va;
-                            sg += inc ? vb : va;
-                            d += inc;
-                            bits |= static_cast<uint32_t>(inc) << (h - 1);
-                            mg.step(fmaf(sg, nm.rs[1][h - 1], -nm.murs[1][h - 1]), h);
-                        }
-                    }
+                if (kS) {
+                    ss += sm_ld<T>(w, e);
+                    const float2 c = nrm[0][h - 1];
+                    const float v = fmaf(ss, c.x, -c.y);
+                    if (v > best_s) { best_s = v; bh_s = h; }
+                }
+                if (kG) {
+                    const float va = sm_ld<T>(w, e + d);
+                    const float vb = sm_ld<T>(w, e + d + 1);
+                    const bool inc = vb > va;
+                    sg += inc ? vb : va;
+                    d += inc;
+                    bits |= static_cast<uint32_t>(inc) << (h - 1);
+                    const float2 c = nrm[1][h - 1];
+                    const float v = fmaf(sg, c.x, -c.y);
+                    if (v > best_g) { best_g = v; bh_g = h; }
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[b]);
+            if (lane == 0) mbar_arrive(&empty[cslot]);
+            if (++cslot == R) { cslot = 0; cpar ^= 1u; }
         }
         if (valid && !s_abort) {
             const int64_t o = fbase + n;
             if (kS) {
-                a.s.snr[o] = ms.best;
-                a.s.best_h[o] = static_cast<uint8_t>(ms.bh);
+                a.s.snr[o] = best_s;
+                a.s.best_h[o] = static_cast<uint8_t>(bh_s);
             }
             if (kG) {
-                a.g.snr[o] = mg.best;
-                a.g.best_h[o] = static_cast<uint8_t>(mg.bh);
+                a.g.snr[o] = best_g;
+                a.g.best_h[o] = static_cast<uint8_t>(bh_g);
                 if (a.g.path) store_path(a.g.path, a.path_bytes, o, bits);
             }
         }
-        if (kS && a.s.argmax) consumer_argmax(valid ? argmax_key(ms.best, n) : 0ull, a.s.argmax + s, red, Tn);
-        if (kG && a.g.argmax) consumer_argmax(valid ? argmax_key(mg.best, n) : 0ull, a.g.argmax + s, red, Tn);
+        if (kS && a.s.argmax) consumer_argmax(valid ? argmax_key(best_s, n) : 0ull, a.s.argmax + s, red, Tn);
+        if (kG && a.g.argmax) consumer_argmax(valid ? argmax_key(best_g, n) : 0ull, a.g.argmax + s, red, Tn);
     }
 }
 

@@ -50,16 +50,16 @@ struct Fwd1DArgs {
     int *err;                      // device error word
 };
 
-// Shared-memory staging plan of the window kernel (kernel 2): the orders 1..H of a tile are
-// packed into phases, each phase's windows filling one of `nbuf` ring buffers.
+// Shared-memory staging plan of the window kernel (kernel 2): the (tile, order) sequence of a
+// CTA streams through a ring of `nslot` slots of `slot_bytes` each; order j goes to slot
+// j % nslot and its bulk copy is issued by producer warp j % nprod.
 struct WinPlan {
     int32_t T;                        // fundamentals per tile (= consumer threads)
-    int32_t nphase;                   // phases per tile
-    int32_t nbuf;                     // ring buffers (2..4)
-    int32_t buf_bytes;                // bytes per ring buffer
+    int32_t nslot;                    // ring slots (2..16)
+    int32_t nprod;                    // producer warps (1..8)
+    int32_t slot_bytes;               // bytes per slot (>= the largest order window)
     int64_t extent;                   // readable elements of the input buffer
-    int32_t phase_h0[kMaxH1D + 1];    // phase p covers orders [phase_h0[p], phase_h0[p+1])
-    int32_t off[kMaxH1D];             // byte offset of order h's window (index h-1) in its buffer
+    int64_t pf_chunk;                 // > 0: CTA i first prefetches input bytes [i c, (i+1) c) into L2
 };
 
 // Bytes of the order-h window of a T-fundamental tile: h (T-1) + h + 1 elements plus up to

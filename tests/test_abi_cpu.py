@@ -132,27 +132,37 @@ def test_tuning_validation(hs):
     p = plan(hs, H=8, forms=3, lengths=[10000])
     t = p.tuning
     assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
-    assert t.kernel == 2 and t.stages >= 2
+    assert t.kernel == 0 and t.threads == 128
     p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
     assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1,
-                                      stages=0, stage_kb=0)
-    p.tuning = dict(kernel=2, threads=256, stages=2, stage_kb=96)
+                                      stages=0, stage_kb=0, prefetch=0, producers=0)
+    with pytest.raises(hs.HSError):      # L2 prefetch belongs to the window kernel
+        p.tuning = dict(kernel=0, threads=128, prefetch=1)
+    p.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=24, prefetch=1, producers=2)
+    p.tuning = dict(kernel=2, threads=256, stages=2, stage_kb=96, producers=1)
     big = plan(hs, H=32, forms=3, lengths=[100000])
     with pytest.raises(hs.HSError):      # order-32 window of a 256-wide tile needs ~32 KiB
-        big.tuning = dict(kernel=2, threads=256, stages=4, stage_kb=24)
+        big.tuning = dict(kernel=2, threads=256, stages=4, stage_kb=24, producers=2)
     with pytest.raises(hs.HSError):      # more than 227 KiB of shared memory
-        big.tuning = dict(kernel=2, threads=128, stages=4, stage_kb=64)
+        big.tuning = dict(kernel=2, threads=128, stages=16, stage_kb=17, producers=4)
+    with pytest.raises(hs.HSError):      # more producer warps than slots
+        big.tuning = dict(kernel=2, threads=128, stages=4, stage_kb=17, producers=5)
+    with pytest.raises(hs.HSError):      # more than 640 threads
+        big.tuning = dict(kernel=2, threads=512, stages=3, stage_kb=66, producers=5)
+    big.tuning = dict(kernel=2, threads=512, stages=3, stage_kb=66, producers=3)
     white = plan(hs, H=8, forms=3, lengths=[1000, 1000], flags=hs.FLAG_WHITENING)
     assert white.tuning.kernel == 1
     with pytest.raises(hs.HSError) as e:
-        white.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=16)
+        white.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=16, producers=1)
     assert e.value.status == 2
     for bad in (dict(kernel=2, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
                 dict(kernel=0, threads=100, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
                 dict(kernel=0, threads=512, fund_per_thread=1, ctas_per_sm=0, dynamic=0),
+                dict(kernel=2, threads=544, stages=2, stage_kb=80, producers=1),
                 dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=1),
-                dict(kernel=2, threads=128, stages=1, stage_kb=48),
-                dict(kernel=2, threads=128, stages=5, stage_kb=8)):
+                dict(kernel=2, threads=128, stages=1, stage_kb=48, producers=1),
+                dict(kernel=2, threads=128, stages=17, stage_kb=8, producers=1),
+                dict(kernel=2, threads=128, stages=4, stage_kb=8, producers=0)):
         with pytest.raises(hs.HSError):
             p.tuning = bad
 

@@ -87,10 +87,11 @@ TUNINGS = [dict(kernel=0, threads=256),
            dict(kernel=1, threads=128, ctas_per_sm=2),
            dict(kernel=0, threads=64, ctas_per_sm=1, dynamic=1),
            dict(kernel=1, threads=192, ctas_per_sm=3, dynamic=1),
-           dict(kernel=2, threads=128, stages=4, stage_kb=48),
-           dict(kernel=2, threads=64, stages=2, stage_kb=16, ctas_per_sm=3),
-           dict(kernel=2, threads=256, stages=2, stage_kb=96, ctas_per_sm=1),
-           dict(kernel=2, threads=96, stages=3, stage_kb=20, ctas_per_sm=2)]
+           dict(kernel=2, threads=128, stages=12, stage_kb=17, producers=4),
+           dict(kernel=2, threads=64, stages=4, stage_kb=9, producers=2, ctas_per_sm=3),
+           dict(kernel=2, threads=256, stages=6, stage_kb=33, producers=6, ctas_per_sm=1, prefetch=1),
+           dict(kernel=2, threads=96, stages=3, stage_kb=13, producers=1, ctas_per_sm=2),
+           dict(kernel=2, threads=448, stages=3, stage_kb=57, producers=3)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
