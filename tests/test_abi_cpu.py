@@ -151,7 +151,7 @@ def test_tuning_validation(hs):
         big.tuning = dict(kernel=2, threads=512, stages=3, stage_kb=66, producers=5)
     big.tuning = dict(kernel=2, threads=512, stages=3, stage_kb=66, producers=3)
     white = plan(hs, H=8, forms=3, lengths=[1000, 1000], flags=hs.FLAG_WHITENING)
-    assert white.tuning.kernel == 1
+    assert white.tuning.kernel == 0
     with pytest.raises(hs.HSError) as e:
         white.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=16, producers=1)
     assert e.value.status == 2
