@@ -162,6 +162,20 @@ hs_status hs_backward(hs_plan plan, int32_t form, const float *grad_snr, const h
                       const void *spectra, const float *w, float *grad_in, float *grad_w,
                       void *workspace, void *stream);
 
+/* Forward pass for callers that cannot allocate device memory (the paper has no counterpart).
+ * Same inputs, outputs and results as hs_run, but the scratch hs_run takes as `workspace` (the
+ * tile counter of the dynamic schedule) is a fixed 4096-byte array inside the library, held on
+ * every GPU that loads the library until the process exits.  Plans needing more workspace than
+ * that get HS_ERR_UNSUPPORTED.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
+ * library call.  The first call on a device looks up the array's device address once (with
+ * that device current); make that first call before any stream capture.  All calls share the
+ * one array and it keeps the last call's contents (the counter is cleared on the stream before
+ * every launch), so calls whose work overlaps on the GPU -- on different streams, or of
+ * different plans -- race and must be serialised by the caller.  HS_FLAG_GRAPH is ignored here
+ * (the work is always launched directly). */
+hs_status hs_run_fixed_scratch(hs_plan plan, const void *spectra, const float *w, const hs_form_io *simple,
+                               const hs_form_io *greedy, void *stream);
+
 /* Synchronises `stream`, then reads and clears the plan's device error word. */
 hs_status hs_check_device_error(hs_plan plan, void *stream);
 

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "backward", "norm_exponential",
+__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_fixed_scratch", "backward", "norm_exponential",
            "check_device_error", "decode_argmax", "status_string", "SIMPLE", "GREEDY", "F32", "F16", "BF16",
            "FLAG_NO_MITIGATION", "FLAG_PER_SPECTRUM_NORM", "FLAG_WHITENING", "FLAG_AUTOTUNE", "FLAG_GRAPH",
            "FLAG_NO_DEVICE", "FLAG_CHECKED", "lib", "LIB_PATH"]
@@ -95,6 +95,7 @@ def lib():
         L.hs_plan_set_tuning.argtypes = [_V, ctypes.POINTER(Tuning)]
         L.hs_run.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V, _V]
         L.hs_backward.argtypes = [_V, _I32, _V, ctypes.POINTER(_FormIO), _V, _V, _V, _V, _V, _V]
+        L.hs_run_fixed_scratch.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V]
         L.hs_check_device_error.argtypes = [_V, _V]
         L.hs_norm_exponential.argtypes = [_I32, _I32, _I32, _I32, ctypes.c_double, _V, _V]
         L.hs_status_string.argtypes = [ctypes.c_int]
@@ -103,7 +104,8 @@ def lib():
         L.hs_version.restype = ctypes.c_char_p
         for name in ("hs_plan_create", "hs_plan_destroy", "hs_plan_fundamentals", "hs_plan_input_offsets",
                      "hs_plan_domain_2d", "hs_plan_workspace", "hs_plan_get_tuning", "hs_plan_set_tuning",
-                     "hs_run", "hs_backward", "hs_check_device_error", "hs_norm_exponential"):
+                     "hs_run", "hs_backward", "hs_check_device_error", "hs_norm_exponential",
+                     "hs_run_fixed_scratch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -311,6 +313,17 @@ def run(plan: Plan, spectra, w=None, simple: FormIO | None = None, greedy: FormI
     cg = greedy._c() if greedy is not None else None
     _check(lib().hs_run(plan.handle, _ptr(spectra), _ptr(w), ctypes.byref(cs) if cs else None,
                         ctypes.byref(cg) if cg else None, _ptr(ws), _stream_ptr(stream)), "hs_run")
+
+
+def run_fixed_scratch(plan: Plan, spectra, w=None, simple: FormIO | None = None, greedy: FormIO | None = None,
+                      stream=None):
+    """hs_run_fixed_scratch: the forward without a workspace, for callers that cannot allocate
+    device memory; its scratch is a fixed array inside the library shared by every call, so calls
+    that overlap on the GPU must be serialised by the caller."""
+    cs = simple._c() if simple is not None else None
+    cg = greedy._c() if greedy is not None else None
+    _check(lib().hs_run_fixed_scratch(plan.handle, _ptr(spectra), _ptr(w), ctypes.byref(cs) if cs else None,
+                                      ctypes.byref(cg) if cg else None, _stream_ptr(stream)), "hs_run_fixed_scratch")
 
 
 def backward(plan: Plan, form: int, grad_snr, fwd: FormIO, spectra=None, w=None, grad_in=None, grad_w=None,

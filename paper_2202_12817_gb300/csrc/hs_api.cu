@@ -864,4 +864,66 @@ hs_status hs_check_device_error(hs_plan p, void *stream)
     return HS_OK;
 }
 
+// -----------------------------------------------------------------------------------------
+// Forward pass without any caller-provided workspace.
+//
+// Some callers cannot allocate device memory at the point where they run the harmonic sum:
+// plug-ins whose host framework owns every allocation, real-time pipelines that forbid
+// allocation after start-up, and code that only receives input and output pointers.  For
+// them the scratch the forward needs (the tile counter of the dynamic schedule) lives in
+// the fixed array below, which the library's module holds on every GPU that loads it until
+// the process exits.  In host code `g_fixed_scratch` names a host-side stand-in, not a device
+// address, so its device address is looked up once per device (cudaGetSymbolAddress, with
+// that device current) and passed to the kernels.
+// -----------------------------------------------------------------------------------------
+constexpr size_t kFixedScratchBytes = 4096;
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
+
+namespace {
+constexpr int kMaxFixedDevices = 64;
+std::mutex g_fixed_mu;
+void *g_fixed_ptr[kMaxFixedDevices] = {};
+
+// Device address of g_fixed_scratch on `device` (looked up on the first call for the device).
+hs_status fixed_scratch_ptr(int device, void **out)
+{
+    if (device < 0 || device >= kMaxFixedDevices) return HS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_fixed_mu);
+    if (!g_fixed_ptr[device]) {
+        DeviceGuard guard(device);
+        if (!guard.ok) return HS_ERR_CUDA;
+        void *ptr = nullptr;
+        HS_CUDA(cudaGetSymbolAddress(&ptr, g_fixed_scratch));
+        g_fixed_ptr[device] = ptr;
+    }
+    *out = g_fixed_ptr[device];
+    return HS_OK;
+}
+}  // namespace
+
+hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
+                               const hs_form_io *greedy, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    size_t need = 0;
+    hs_plan_workspace(p, &need);
+    if (need > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;   // plan needs more scratch than the array
+    if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
+    if (w && !aligned(w, 16)) return HS_ERR_INVALID_ARG;
+    const bool want_s = (p->d.forms & HS_FORM_SIMPLE) != 0, want_g = (p->d.forms & HS_FORM_GREEDY) != 0;
+    if (want_s != (simple != nullptr) || want_g != (greedy != nullptr)) return HS_ERR_INVALID_ARG;
+    if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
+    if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
+    void *scratch = nullptr;
+    hs_status st = fixed_scratch_ptr(p->device, &scratch);
+    if (st != HS_OK) return st;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(p->mu);
+    return enqueue_fwd(p, spectra, w, simple, greedy, scratch, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"
