@@ -1,12 +1,24 @@
 #!/usr/bin/env python3
 """Throughput of the GB300 harmonic sum (bins x harmonics / s) against the HBM roofline.
 
-Default workload (one step = one fused simple + greedy pass): a single FP32 power spectrum of
-2^23 bins, H = 32, Exponential(1) noise with 16 injected pulsars (f0 ~ U[100, N/32), duty
-~ U[0.02, 0.2)), 262143 fundamentals.  L2 is flushed (a 2 x L2 write) before every timed step;
-each step is timed alone with CUDA events on the stream hs_run launches on.
+Default workload (one step = one fused simple + greedy pass, one kernel): a single FP32 power
+spectrum of 2^23 bins, H = 32, Exponential(1) noise with 16 injected pulsars (f0 ~ U[100, N/32),
+duty ~ U[0.02, 0.2)), 262143 fundamentals.  The spectrum (32 MiB) fits in L2, so L2 is flushed
+(a write of max(2 x L2, 256 MiB)) before every timed step, and every step is timed alone with
+CUDA events on the stream hs_run launches on.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload long|long16|batch|plane|grad]
+Other workloads (--workload), each one JSON line of the same shape:
+  long16 / longbf16   the same spectrum stored in FP16 / BF16 (FP32 accumulation)
+  batch / batch16     2048 uneven spectra (2^20..2^23 bins), H = 16, 5 % with a pulsar, one
+                      persistent launch replayed from a CUDA graph, launch shape autotuned;
+                      FP32 / FP16 storage (inputs 32 / 16 GB, larger than L2: no flush)
+  plane               2D greedy over an f-fdot plane 201 x 2^21 (z = -100..100), H = 8,
+                      chi-square(2) noise + 8 drifting signals (1.69 GB, larger than L2)
+  grad                one training step of a learnable per-bin whitening: 256 spectra x 2^20
+                      bins, H = 32, greedy forward, loss = -sum of the top-16 SNRs per spectrum
+                      (torch.topk), hand-written adjoint to dL/dw
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ...]
     python bench.py --impl reference      # the FP64 oracle on the host cores, same metric
 
 N > 1 (torchrun): replicas only -- every rank runs the whole workload on its own GPU (the
@@ -35,8 +47,8 @@ METRIC = "bins×harmonics/s and HBM GB/s (% of peak), greedy vs simple HS at H=3
 UNIT = "bins*harmonics/s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "footprints.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_fwd1d_f16.cu", "hs_fwd1d_bf16.cu", "hs_fwd2d.cu",
-                  "hs_bwd1d.cu", "hs_internal.cuh", "hs_api.cu"]
+KERNEL_SOURCES = ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f32.cu", "hs_fwd1d_f16.cu", "hs_fwd1d_bf16.cu",
+                  "hs_fwd2d.cu", "hs_bwd1d.cu", "hs_internal.cuh", "hs_api.cu"]
 
 
 def log(*a):
@@ -127,25 +139,43 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # oracle timing (CPU baseline / reference arm): the only place bench.py runs oracle/
 # ---------------------------------------------------------------------------------------------
-def oracle_rate(x_host, H, budget_s=8.0, frac=1.0):
-    """Time the FP64 single-thread oracle (simple + greedy) on the first ``frac`` of the
+def oracle_rate_1d(x_host, H, budget_s=8.0, frac=1.0, forms=3):
+    """Time the FP64 single-thread oracle (simple and/or greedy) on the first ``frac`` of the
     spectrum's fundamentals, repeated until ``budget_s``; returns (units/s, sample text)."""
     import oracle
     oracle.build()
-    nf_all = oracle.nf_1d(x_host.size, H)
-    nf = max(1, int(nf_all * frac))
+    nf = max(1, int(oracle.nf_1d(x_host.size, H) * frac))
     mu_s, sg_s = oracle.norm_exponential(1, 1, H)
     mu_g, sg_g = oracle.norm_exponential(2, 1, H)
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.simple_1d(x_host, H, mu_s, sg_s, nf=nf)
-        oracle.greedy_1d(x_host, H, mu_g, sg_g, nf=nf)
+        if forms & 1:
+            oracle.simple_1d(x_host, H, mu_s, sg_s, nf=nf)
+        if forms & 2:
+            oracle.greedy_1d(x_host, H, mu_g, sg_g, nf=nf)
         reps += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    units = reps * nf * H
-    return units / el, f"{reps} x fundamentals [0, {nf}) of the {x_host.size}-bin spectrum, simple + greedy, 1 thread"
+    what = {1: "simple", 2: "greedy", 3: "simple + greedy"}[forms]
+    return reps * nf * H / el, f"{reps} x fundamentals [0, {nf}) of a {x_host.size}-bin spectrum, {what}, 1 thread"
+
+
+def oracle_rate_2d(plane_host, z0_row, H, budget_s=8.0, z_rows=1):
+    import oracle
+    oracle.build()
+    f_lo, f_hi, z_lo, z_hi = oracle.domain_2d(plane_host.shape[1], plane_host.shape[0], z0_row, H)
+    dom = (f_lo, f_hi, 0, z_rows - 1)
+    mu, sg = oracle.norm_exponential(2, 2, H, mean1=2.0)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.greedy_2d(plane_host, z0_row, H, mu, sg, dom=dom)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    units = reps * (f_hi - f_lo + 1) * z_rows * H
+    return units / el, f"{reps} x z in [0, {z_rows}) x all {f_hi - f_lo + 1} f of the plane, 1 thread"
 
 
 # ---------------------------------------------------------------------------------------------
@@ -176,60 +206,79 @@ def max_over_ranks(v, dist, device):
 
 
 # ---------------------------------------------------------------------------------------------
-# workloads
+# compulsory bytes
 # ---------------------------------------------------------------------------------------------
-def algorithmic_bytes_1d(n_bins, H, forms, elem, nf, B=1, key="long"):
-    """Compulsory bytes of one pass: distinct 32-B input sectors read (oracle-counted for the
-    benchmark spectrum, stored in tests/golden/footprints.json; else the whole input) + outputs
-    (snr 4 B + best_h 1 B per form, greedy path 4 B for H > 16) + mu/sigma tables."""
-    gold = load_json(GOLDEN) or {}
-    fp = gold.get(key, {}).get({1: "simple", 2: "greedy", 3: "fused"}[forms])
-    if fp is not None and elem == 4:
-        in_bytes, how = int(fp["sectors"]) * 32, "oracle sector footprint"
-    elif fp is not None:
-        in_bytes, how = int(fp["sectors_16bit"]) * 32, "oracle sector footprint"
-    else:
-        in_bytes, how = n_bins * elem, "whole input"
+def out_bytes_1d(nf, H, forms):
     pb = 4 if H > 16 else (2 if H > 8 else 1)
-    out = 0
+    b = 0
     if forms & 1:
-        out += nf * 5
+        b += nf * 5
     if forms & 2:
-        out += nf * (5 + pb)
-    norms = 2 * 4 * H * (2 if forms == 3 else 1) * B
-    return in_bytes + out + norms, how
+        b += nf * (5 + pb)
+    return b
 
 
-def run_device(args, hs, torch, dev, rank, world, dist):
+def long_alg_bytes(H, forms, elem, nf):
+    """Compulsory bytes of one pass over the benchmark spectrum: its distinct 32-B sectors that
+    the forms read (oracle-counted, tests/golden/footprints.json) + outputs + mu/sigma."""
+    gold = (load_json(GOLDEN) or {}).get("long", {})
+    fp = gold.get({1: "simple", 2: "greedy", 3: "fused"}[forms])
+    if fp is not None:
+        in_bytes, how = int(fp["sectors" if elem == 4 else "sectors_16bit"]) * 32, "oracle sector footprint"
+    else:
+        in_bytes, how = synth.LONG_N * elem, "whole input"
+    return in_bytes + out_bytes_1d(nf, H, forms) + 2 * 4 * H * (2 if forms == 3 else 1), how
+
+
+def batch_alg_bytes(lengths, H, elem, nf):
+    gold = (load_json(GOLDEN) or {}).get("batch_H16_fraction", {})
+    key = "fused" if elem == 4 else "fused_16bit"
+    tot, how = 0.0, "oracle sector footprint per length"
+    for n in lengths:
+        fr = gold.get(str(int(n)), {}).get(key)
+        if fr is None:
+            fr, how = 1.0, "whole input"
+        tot += fr * n * elem
+    return int(tot) + out_bytes_1d(nf, H, 3) + 4 * 4 * H, how
+
+
+# ---------------------------------------------------------------------------------------------
+# timing helper
+# ---------------------------------------------------------------------------------------------
+def time_steps(torch, step, K, stream, flush=None):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        if flush is not None:
+            flush.fill_(float(i & 7))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def roofline(alg_bytes, ms, peak, peak_kind, wl, how):
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    prof = load_json(PROFILE_TRAFFIC) or {}
+    pk = prof.get(wl) or {}
+    fresh = pk.get("kernel_hash") == kernel_hash()
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": pk.get("dram_bytes_per_launch") if fresh else None,
+            "algorithmic_bytes": int(alg_bytes), "bytes_basis": how, "peak_kind": peak_kind,
+            "kernel": pk.get("kernel") if fresh else None}
+
+
+# ---------------------------------------------------------------------------------------------
+# workloads: each returns (result dict without clocks, clock summary, cpu-baseline function)
+# ---------------------------------------------------------------------------------------------
+def wl_long(args, hs, torch, dev, world, dist):
     wl = args.workload
     H = 32
-    elem = 4
-    dtype = hs.F32
-    if wl in ("long", "long16", "longbf16"):
-        N = synth.LONG_N
-        dtype = {"long": hs.F32, "long16": hs.F16, "longbf16": hs.BF16}[wl]
-        elem = 4 if dtype == hs.F32 else 2
-        x32 = synth.device_spectrum(N, synth.SEED_BASE + 2, synth.long_spectrum_pulsars(), dev)
-        x = x32 if dtype == hs.F32 else x32.to(torch.float16 if dtype == hs.F16 else torch.bfloat16)
-        lengths = [N]
-        desc = f"single FP32 spectrum 2^23 bins, H=32, 16 pulsars" if dtype == hs.F32 else \
-            f"single spectrum 2^23 bins stored {'FP16' if dtype == hs.F16 else 'BF16'}, H=32"
-        host_for_oracle = x32
-    elif wl == "batch":
-        H = 16
-        b = synth.uneven_batch()
-        x = synth.device_batch(b, dev)
-        lengths = list(b.lengths)
-        desc = "2048 uneven FP32 spectra (2^20..2^23 bins), H=16, 5% with a pulsar"
-        host_for_oracle = None
-    else:
-        raise SystemExit(f"unknown workload {wl}")
-    flags = hs.FLAG_GRAPH if wl == "batch" else 0
-    offsets = None
-    if wl == "batch":
-        offsets = b.offsets[:-1]
-    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=lengths, dtype=dtype, offsets=offsets, flags=flags,
-                   device=dev.index)
+    dtype = {"long": hs.F32, "long16": hs.F16, "longbf16": hs.BF16}[wl]
+    elem = 4 if dtype == hs.F32 else 2
+    x32 = synth.device_spectrum(synth.LONG_N, synth.SEED_BASE + 2, synth.long_spectrum_pulsars(), dev)
+    x = x32 if dtype == hs.F32 else x32.to(torch.float16 if dtype == hs.F16 else torch.bfloat16)
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=[synth.LONG_N], dtype=dtype, device=dev.index)
     if args.tuning:
         plan.tuning = json.loads(args.tuning)
     nf = plan.total_fundamentals
@@ -249,107 +298,251 @@ def run_device(args, hs, torch, dev, rank, world, dist):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize(dev)
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(dev.index) as clk:
         t0 = time.perf_counter()
-        for i in range(K):
-            flush.fill_(float(i & 7))
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize(dev)
+        times = time_steps(torch, step, args.steps, stream, flush)
         wall = time.perf_counter() - t0
     if dist:
         dist.barrier()
-    times = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(times) / K
+    ms = sum(times) / len(times)
     ms_max = max_over_ranks(ms, dist, dev)
     units = nf * H
-    value = world * units / (ms_max / 1e3)
-    fkey = "long" if wl.startswith("long") else wl
-    alg, how = algorithmic_bytes_1d(plan.extent, H, 3, elem, nf, plan.B, key=fkey)
     peak, peak_kind = measured_peaks()
-    achieved = alg / (ms / 1e3) / 1e9
-    prof = load_json(PROFILE_TRAFFIC) or {}
-    traffic = None
-    pk = prof.get(wl)
-    if pk and pk.get("kernel_hash") == kernel_hash():
-        traffic = pk.get("dram_bytes_per_launch")
+    alg, how = long_alg_bytes(H, 3, elem, nf)
 
-    # per-form separate passes (simple only, greedy only) on the same input
+    # each form alone (separate plans, same input), reported beside the fused pass
     per_form = {}
     for form, name in ((hs.SIMPLE, "simple"), (hs.GREEDY, "greedy")):
-        p2 = hs.Plan(H, form, lengths=lengths, dtype=dtype, offsets=offsets, device=dev.index)
+        p2 = hs.Plan(H, form, lengths=[synth.LONG_N], dtype=dtype, device=dev.index)
         if args.tuning:
             p2.tuning = json.loads(args.tuning)
         io = p2.alloc_form(*(ns if form == hs.SIMPLE else ng), path=form == hs.GREEDY, argmax=True)
         ws2 = p2.workspace(dev)
+
+        def st2():
+            hs.run(p2, x, None, io if form == 1 else None, io if form == 2 else None, ws2, stream)
+
         for _ in range(3):
             flush.fill_(1.0)
-            hs.run(p2, x, None, io if form == 1 else None, io if form == 2 else None, ws2, stream)
-        reps = min(K, 200)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        for i in range(reps):
-            flush.fill_(float(i & 7))
-            evs[i][0].record(stream)
-            hs.run(p2, x, None, io if form == 1 else None, io if form == 2 else None, ws2, stream)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize(dev)
-        fms = sum(a.elapsed_time(b) for a, b in evs) / reps
-        fb, _ = algorithmic_bytes_1d(plan.extent, H, form, elem, nf, plan.B, key=fkey)
+            st2()
+        ft = time_steps(torch, st2, min(args.steps, 300), stream, flush)
+        fms = sum(ft) / len(ft)
+        fb, _ = long_alg_bytes(H, form, elem, nf)
         per_form[name] = {"value": units / (fms / 1e3), "ms": round(fms, 5),
-                          "hbm_gbs": round(fb / (fms / 1e3) / 1e9, 1),
-                          "frac": round(fb / (fms / 1e3) / 1e9 / peak, 4)}
+                          "hbm_gbs": round(fb / (fms / 1e3) / 1e9, 1), "frac": round(fb / (fms / 1e3) / 1e9 / peak, 4),
+                          "tuning": p2.tuning.as_dict()}
         p2.close()
 
     # end to end through the C ABI with host buffers: pinned H2D of the spectrum, run,
     # D2H of every output, all inside the timed region
     xh = x.cpu().pin_memory()
-    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in
-              (s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax)]
+    dev_outs = (s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax)
+    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in dev_outs]
     xd2 = torch.empty_like(x)
-    e_reps = max(3, min(K, 20))
-    for i in range(e_reps + 2):
-        if i == 2:
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+
+    def e2e_step():
         xd2.copy_(xh, non_blocking=True)
         hs.run(plan, xd2, None, s_io, g_io, ws, stream)
-        for hbuf, dbuf in zip(outs_h, (s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path,
-                                       g_io.argmax)):
+        for hbuf, dbuf in zip(outs_h, dev_outs):
             hbuf.copy_(dbuf, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e_ms = max_over_ranks(e0.elapsed_time(e1) / e_reps, dist, dev)
-    h2d = x.numel() * x.element_size()
-    d2h = sum(t.numel() * t.element_size() for t in outs_h)
+
+    for _ in range(2):
+        e2e_step()
+    et = time_steps(torch, e2e_step, max(3, min(args.steps, 30)), stream)
+    e_ms = max_over_ranks(sum(et) / len(et), dist, dev)
 
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {hs.F32: "f32", hs.F16: "f16 storage, f32 accumulate",
-                  hs.BF16: "bf16 storage, f32 accumulate"}[dtype],
+        "metric": METRIC, "value": world * units / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {hs.F32: "f32", hs.F16: "f16 storage, f32 accumulate", hs.BF16: "bf16 storage, f32 accumulate"}[dtype],
         "data": "synthetic",
-        "config": {"workload": desc, "bins": int(plan.extent), "H": H, "fundamentals": int(nf),
-                   "forms": "simple+greedy fused (one kernel)", "parallelism": "replicas" if world > 1 else "1 GPU",
+        "config": {"workload": "single spectrum of 2^23 bins (%s), H=32, 16 pulsars, simple+greedy fused"
+                               % {hs.F32: "FP32", hs.F16: "FP16", hs.BF16: "BF16"}[dtype],
+                   "bins": synth.LONG_N, "H": H, "fundamentals": int(nf),
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed before every timed step (write of max(2 x L2, 256 MiB))",
                    "tuning": plan.tuning.as_dict()},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "algorithmic_bytes": int(alg), "bytes_basis": how, "peak_kind": peak_kind},
+        "roofline": roofline(alg, ms, peak, peak_kind, wl, how),
         "per_form": per_form,
-        "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": K,
-        "wall_s_timed_region": round(wall, 3),
+        "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(x.numel() * x.element_size()),
+                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in outs_h))},
+        "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 3),
     }
-    return result, clk.summary(), host_for_oracle
+    xs_host = x.float().cpu().numpy()
+    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0)
+
+
+def wl_batch(args, hs, torch, dev, world, dist):
+    H = 16
+    dtype = hs.F16 if args.workload == "batch16" else hs.F32
+    elem = 4 if dtype == hs.F32 else 2
+    b = synth.uneven_batch()
+    x = synth.device_batch(b, dev, dtype=torch.float16 if dtype == hs.F16 else None)
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=b.lengths, dtype=dtype, offsets=b.offsets[:-1],
+                   flags=hs.FLAG_GRAPH | (0 if args.tuning else hs.FLAG_AUTOTUNE), device=dev.index)
+    if args.tuning:
+        plan.tuning = json.loads(args.tuning)
+    nf = plan.total_fundamentals
+    ns = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.SIMPLE, 1, H)]
+    ng = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
+    s_io = plan.alloc_form(*ns, path=False, argmax=True)
+    g_io = plan.alloc_form(*ng, path=True, argmax=True)
+    ws = plan.workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hs.run(plan, x, None, s_io, g_io, ws, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    steps = min(args.steps, 40)
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        times = time_steps(torch, step, steps, stream)
+        wall = time.perf_counter() - t0
+    ms = sum(times) / len(times)
+    ms_max = max_over_ranks(ms, dist, dev)
+    peak, peak_kind = measured_peaks()
+    alg, how = batch_alg_bytes(b.lengths, H, elem, nf)
+    result = {
+        "metric": METRIC, "value": world * nf * H / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == hs.F32 else "f16 storage, f32 accumulate",
+        "data": "synthetic",
+        "config": {"workload": f"2048 uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
+                               "H=16, 5% with a pulsar, one persistent launch from a CUDA graph",
+                   "bins": int(sum(b.lengths)), "H": H, "fundamentals": int(nf), "spectra": len(b.lengths),
+                   "l2": "inputs larger than L2 (no flush)", "tuning": plan.tuning.as_dict()},
+        "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how),
+        "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
+    }
+    i0 = int(np.argmax(b.lengths))
+    xs_host = synth.batch_trial(b, i0)
+    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0)
+
+
+def wl_plane(args, hs, torch, dev, world, dist):
+    H = 8
+    tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
+    pl = synth.device_plane(synth.PLANE_N_FREQ, synth.PLANE_N_ROWS, synth.PLANE_Z0_ROW, synth.SEED_BASE + 4,
+                            tracks, dev)
+    plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=synth.PLANE_N_FREQ, n_rows=synth.PLANE_N_ROWS,
+                   z0_row=synth.PLANE_Z0_ROW, device=dev.index)
+    nfund = plan.total_fundamentals
+    ng = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 2, H, True, 2.0)]
+    g_io = plan.alloc_form(*ng, path=True, argmax=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hs.run(plan, pl, None, None, g_io, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    steps = min(args.steps, 200)
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        times = time_steps(torch, step, steps, stream)
+        wall = time.perf_counter() - t0
+    ms = sum(times) / len(times)
+    ms_max = max_over_ranks(ms, dist, dev)
+    peak, peak_kind = measured_peaks()
+    gold = (load_json(GOLDEN) or {}).get("plane", {})
+    if "sectors" in gold:
+        alg, how = int(gold["sectors"]) * 32, "oracle sector footprint"
+    else:
+        alg, how = synth.PLANE_N_FREQ * synth.PLANE_N_ROWS * 4, "whole input"
+    alg += nfund * (4 + 1 + 4) + 2 * 4 * H
+    result = {
+        "metric": METRIC, "value": world * nfund * H / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2D greedy over an f-fdot plane 201 x 2^21 (FP32), H=8, 8 drifting signals",
+                   "fundamentals": int(nfund), "H": H, "domain": list(plan.domain),
+                   "l2": "input larger than L2 (no flush)"},
+        "roofline": roofline(alg, ms, peak, peak_kind, "plane", how),
+        "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
+    }
+    host_plane = pl.cpu().numpy()
+    return result, clk.summary(), lambda: oracle_rate_2d(host_plane, synth.PLANE_Z0_ROW, H, budget_s=10.0)
+
+
+def wl_grad(args, hs, torch, dev, world, dist):
+    B, N, H, K = 256, 1 << 20, 32, 16
+    p = torch.empty(B * N, dtype=torch.float32, device=dev)
+    for i in range(B):
+        view = p[i * N:(i + 1) * N]
+        synth.device_noise(N, synth.SEED_BASE + 5 + 7 * i, dev, out=view)
+        synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 5000 + i)[0]])
+    w = torch.ones(N, dtype=torch.float32, device=dev, requires_grad=True)
+    plan = hs.Plan(H, hs.GREEDY, lengths=[N] * B, flags=hs.FLAG_WHITENING, device=dev.index)
+    mu, sg = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
+    nf = plan.total_fundamentals // B
+    stream = torch.cuda.current_stream(dev)
+    fwd_t, bwd_t = [], []
+
+    def step(timed=False):
+        w.grad = None
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        snr, bh, path = hs.HarmonicSum.apply(p, w, plan, hs.GREEDY, mu, sg)
+        loss = -snr.view(B, nf).topk(K, dim=1).values.sum()
+        e1.record(stream)
+        loss.backward()
+        e2.record(stream)
+        if timed:
+            fwd_t.append((e0, e1))
+            bwd_t.append((e1, e2))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    steps = min(args.steps, 100)
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step(True)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    f_ms = sum(a.elapsed_time(b) for a, b in fwd_t) / steps
+    b_ms = sum(a.elapsed_time(b) for a, b in bwd_t) / steps
+    ms = f_ms + b_ms
+    ms_max = max_over_ranks(ms, dist, dev)
+    units = B * nf * H
+    peak, peak_kind = measured_peaks()
+    frac = (load_json(GOLDEN) or {}).get("grad_H32_fraction", {}).get(str(N), {}).get("fused", 1.0)
+    fwd_bytes = B * N * 4 * frac + N * 4 + B * nf * (4 + 1 + 4)
+    bwd_bytes = B * N * 4 + B * nf * (4 + 1 + 4) + N * 4
+    result = {
+        "metric": METRIC, "value": world * units / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "training step: 256 spectra x 2^20 bins, H=32, learnable whitening, greedy "
+                               "forward + top-16 loss (torch.topk) + adjoint to dL/dw", "H": H, "spectra": B,
+                   "fwd_ms": round(f_ms, 4), "bwd_ms": round(b_ms, 4), "l2": "inputs larger than L2 (no flush)",
+                   "tuning": plan.tuning.as_dict()},
+        "roofline": roofline(fwd_bytes + bwd_bytes, ms, peak, peak_kind, "grad",
+                             "fwd: oracle sector fraction x input + w + outputs; bwd: input + forward outputs + dL/dw"),
+        "gpu_launches": 2 * steps, "wall_s_timed_region": round(wall, 3),
+    }
+    xs_host = p[:N].cpu().numpy()
+    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0, forms=2)
+
+
+WORKLOADS = {"long": wl_long, "long16": wl_long, "longbf16": wl_long, "batch": wl_batch, "batch16": wl_batch,
+             "plane": wl_plane, "grad": wl_grad}
 
 
 def main():
@@ -358,16 +551,16 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="long", choices=["long", "long16", "longbf16", "batch"])
+    ap.add_argument("--workload", default="long", choices=sorted(WORKLOADS))
     ap.add_argument("--tuning", default=None, help="JSON hs_tuning override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
 
     if args.impl == "reference":
-        # the FP64 oracle on the host cores; under torchrun only rank 0 works
+        # the FP64 oracle on the host cores, each step a bounded sample (1/32 of the fundamentals)
+        # of the default workload; under torchrun only rank 0 works
         if rank != 0:
             return
         H = 32
@@ -376,19 +569,18 @@ def main():
         nf = oracle.nf_1d(x.size, H)
         frac = 1.0 / 32
         for _ in range(args.warmup):
-            oracle_rate(x, H, budget_s=0.0, frac=frac / 4)
+            oracle_rate_1d(x, H, budget_s=0.0, frac=frac / 4)
         t0 = time.perf_counter()
-        units = 0
         for _ in range(args.steps):
-            r, sample = oracle_rate(x, H, budget_s=0.0, frac=frac)
-            units += int(nf * frac) * H
+            oracle_rate_1d(x, H, budget_s=0.0, frac=frac)
         el = time.perf_counter() - t0
-        v = units / el
+        v = args.steps * int(nf * frac) * H / el
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single FP32 spectrum 2^23 bins, H=32, 16 pulsars", "H": H},
+            "config": {"workload": "single spectrum of 2^23 bins (FP32), H=32, 16 pulsars, simple+greedy fused",
+                       "H": H},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: fundamentals [0, {int(nf * frac)}) of the 2^23-bin spectrum, "
                                        "simple + greedy, single-thread FP64"},
@@ -400,11 +592,10 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     dist = init_dist(world, "nccl")
-    result, clocks, host_src = run_device(args, hs, torch, dev, rank, world, dist)
+    result, clocks, cpu_fn = WORKLOADS[args.workload](args, hs, torch, dev, world, dist)
     result["clocks"] = clocks
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and host_src is not None:
-        xh = host_src.cpu().numpy()
-        v, sample = oracle_rate(xh, result["config"]["H"], budget_s=10.0)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = cpu_fn()
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     elif rank == 0:
         result["cpu_baseline"] = None

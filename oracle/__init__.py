@@ -16,6 +16,7 @@ The arithmetic lives in ``hs_oracle.c`` (plain C, FP64, single thread), compiled
   dp_1d       optimal partial sums over all monotone drift paths (Sec. 2.2 drift tree)
   brute_1d/2d exhaustive enumeration of drift paths (tiny inputs)
   sectors_1d  distinct 32-B input sectors read (compulsory input bytes)
+  sectors_2d  the same for the 2D greedy form over an f-fdot plane
   norm_*      closed-form mean / sigma of partial sums of i.i.d. exponential noise
 
 Every function is pinned by ``tests/test_oracle_*.py`` against values the paper or the
@@ -78,6 +79,8 @@ def lib():
             L.hso_brute_2d.argtypes = [_P, _I64, _I64, _I64, _I32, _I64, _I64, _P, _P, _P]
             L.hso_sectors_1d.restype = _I64
             L.hso_sectors_1d.argtypes = [_I32, _I32, _I64, _I32, _I32, _I64, _P]
+            L.hso_sectors_2d.restype = _I64
+            L.hso_sectors_2d.argtypes = [_I64, _I64, _I64, _I32, _I64, _I64, _I64, _I64, _P]
             _lib = L
     return _lib
 
@@ -213,6 +216,16 @@ def sectors_1d(forms, elem_bytes, n, H, path=None, mitigation=True, nf=None):
                              _ptr(path))
     if r < 0:
         raise ValueError("oracle sectors_1d: invalid arguments")
+    return int(r)
+
+
+def sectors_2d(n_freq, n_rows, z0_row, H, path, dom=None):
+    """Distinct 32-B sectors of a float32 plane read by the 2D greedy form along ``path``."""
+    f_lo, f_hi, z_lo, z_hi = dom if dom is not None else domain_2d(n_freq, n_rows, z0_row, H)
+    path = np.ascontiguousarray(path, np.uint32)
+    r = lib().hso_sectors_2d(int(n_freq), int(n_rows), int(z0_row), int(H), f_lo, f_hi, z_lo, z_hi, _ptr(path))
+    if r < 0:
+        raise ValueError("oracle sectors_2d: invalid arguments")
     return int(r)
 
 

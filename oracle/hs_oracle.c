@@ -371,3 +371,38 @@ int64_t hso_sectors_1d(int32_t forms, int32_t elem_bytes, int64_t n, int32_t H,
     free(seen);
     return count;
 }
+
+/*
+ * Distinct 32-byte sectors of the float32 plane read by the 2D greedy form over the domain
+ * [f_lo, f_hi] x [z_lo, z_hi]: the 3x3 neighbourhood of every order along the recorded paths
+ * (path[o], 4 bits per order, output index o as in hso_greedy_2d).
+ */
+int64_t hso_sectors_2d(int64_t n_freq, int64_t n_rows, int64_t z0_row, int32_t H, int64_t f_lo, int64_t f_hi,
+                       int64_t z_lo, int64_t z_hi, const uint32_t *path)
+{
+    if (!path || H < 1 || H > 8 || f_lo < 1 || f_hi < f_lo || z_hi < z_lo) return -1;
+    const int64_t per_row = (n_freq + 7) / 8;
+    const int64_t ns = per_row * n_rows;
+    uint8_t *seen = (uint8_t *)calloc((size_t)((ns + 7) / 8), 1);
+    if (!seen) return -1;
+    int64_t count = 0;
+    const int64_t nff = f_hi - f_lo + 1;
+    for (int64_t z = z_lo; z <= z_hi; ++z)
+        for (int64_t f = f_lo; f <= f_hi; ++f) {
+            const uint32_t bits = path[(z - z_lo) * nff + (f - f_lo)];
+            int64_t df = 0, dz = 0;
+            for (int h = 1; h <= H; ++h) {
+                const int64_t cf = (int64_t)h * f + df, cr = z0_row + (int64_t)h * z + dz;
+                for (int oz = -1; oz <= 1; ++oz)
+                    for (int of = -1; of <= 1; ++of) {
+                        const int64_t s_ = (cr + oz) * per_row + (cf + of) / 8;
+                        if (!(seen[s_ >> 3] & (1u << (s_ & 7)))) { seen[s_ >> 3] |= (uint8_t)(1u << (s_ & 7)); ++count; }
+                    }
+                const int code = (int)((bits >> (4 * (h - 1))) & 0xFu);
+                df += code % 3 - 1;
+                dz += code / 3 - 1;
+            }
+        }
+    free(seen);
+    return count;
+}

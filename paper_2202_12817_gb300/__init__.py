@@ -327,11 +327,13 @@ def run_fixed_scratch(plan: Plan, spectra, w=None, simple: FormIO | None = None,
 
 
 def backward(plan: Plan, form: int, grad_snr, fwd: FormIO, spectra=None, w=None, grad_in=None, grad_w=None,
-             stream=None):
+             workspace=None, stream=None):
     """hs_backward: dL/d(spectra) into ``grad_in`` and/or dL/dw into ``grad_w``."""
     c = fwd._c()
+    if workspace is None and grad_w is not None:
+        workspace = plan.workspace(grad_w.device)
     _check(lib().hs_backward(plan.handle, form, _ptr(grad_snr), ctypes.byref(c), _ptr(spectra), _ptr(w),
-                             _ptr(grad_in), _ptr(grad_w), None, _stream_ptr(stream)), "hs_backward")
+                             _ptr(grad_in), _ptr(grad_w), _ptr(workspace), _stream_ptr(stream)), "hs_backward")
 
 
 def check_device_error(plan: Plan, stream=None):

@@ -34,7 +34,8 @@ bool cuda_ok(cudaError_t e)
 constexpr uint32_t kKnownFlags = HS_FLAG_NO_MITIGATION | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_WHITENING |
                                  HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_NO_DEVICE | HS_FLAG_CHECKED;
 constexpr size_t kWorkspaceBytes = 256;     // tile counter of the dynamic schedule
-constexpr int kBwdBlockBins = 2048;
+constexpr int kBwdBlockBins = 1024;   // must stay <= 32767 (int16 offsets)
+constexpr int kBwdMaxGroups = 16;     // spectrum groups of the adjoint's dL/dw partial sums
 constexpr int kBwdThreads = 256;
 
 int elem_bytes(int dtype) { return dtype == HS_F32 ? 4 : 2; }
@@ -91,6 +92,23 @@ struct hs_plan_s {
 namespace {
 
 int64_t tile_fund(const hs_tuning &t) { return static_cast<int64_t>(t.threads) * t.fund_per_thread; }
+
+// Forward: the dynamic schedule's tile counter (1D).
+size_t fwd_workspace_bytes(const hs_plan p) { return p->d.dims == 1 ? kWorkspaceBytes : 0; }
+
+// Adjoint with dL/dw: spectra are split into groups summed by different CTAs; each group's
+// partial dL/dw (N floats) lives in the workspace and a final pass adds them in order.
+int bwd_groups(const hs_plan p)
+{
+    if (p->d.dims != 1 || !(p->d.flags & HS_FLAG_WHITENING)) return 1;
+    return static_cast<int>(std::min<int64_t>(p->d.num_spectra, kBwdMaxGroups));
+}
+
+size_t bwd_workspace_bytes(const hs_plan p)
+{
+    const int g = bwd_groups(p);
+    return g > 1 ? static_cast<size_t>(g) * static_cast<size_t>(p->len[0]) * sizeof(float) : 0;
+}
 void make_win_plan(hs_plan p);
 
 void compute_tiles(hs_plan p)
@@ -160,6 +178,13 @@ hs_tuning default_tuning(const hs_plan p)
     // kernel for the fused pass; HS_FLAG_AUTOTUNE times the alternatives per plan
     (void)p;
     return hs_tuning{0, 128, 1, 0, 0, 0, 0, 0, 0};
+}
+
+hs_status ensure_bwd_smem(const void *fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return HS_OK;
+    HS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+    return HS_OK;
 }
 
 std::mutex g_attr_mu;
@@ -694,7 +719,7 @@ hs_status hs_plan_domain_2d(hs_plan p, int64_t *f_lo, int64_t *f_hi, int64_t *z_
 hs_status hs_plan_workspace(hs_plan p, size_t *bytes)
 {
     if (!p || !bytes) return HS_ERR_INVALID_ARG;
-    *bytes = p->d.dims == 1 ? kWorkspaceBytes : 0;
+    *bytes = std::max(fwd_workspace_bytes(p), bwd_workspace_bytes(p));
     return HS_OK;
 }
 
@@ -789,7 +814,6 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
                       const void *spectra, const float *w, float *grad_in, float *grad_w,
                       void *workspace, void *stream)
 {
-    (void)workspace;
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
     if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
@@ -826,12 +850,24 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     a.grad_w = grad_w;
     a.n_common = p->len[0];
     a.block_bins = kBwdBlockBins;
+    a.group = 1;
+    a.dw_partial = nullptr;
+    // candidates of a block: sum over k of (floor((L-1)/k) + 2) (greedy), bounded generously
+    int max_cand = 0;
+    for (int k = 1; k <= p->d.H; ++k) max_cand += (kBwdBlockBins - 1) / k + 3;
+    a.max_cand = max_cand;
     a.err = p->d_err;
     int64_t gx;
     int gy;
     if (grad_w) {
         gx = (p->len[0] + kBwdBlockBins - 1) / kBwdBlockBins;
-        gy = 1;
+        gy = bwd_groups(p);
+        a.group = static_cast<int32_t>((B + gy - 1) / gy);
+        gy = static_cast<int>((B + a.group - 1) / a.group);
+        if (gy > 1) {
+            if (!workspace || !aligned(workspace, 16)) return HS_ERR_INVALID_ARG;
+            a.dw_partial = static_cast<float *>(workspace);
+        }
     } else {
         gx = (p->max_len + kBwdBlockBins - 1) / kBwdBlockBins;
         if (B > 65535) return HS_ERR_UNSUPPORTED;
@@ -844,8 +880,23 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
     void *args[] = {&a};
-    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(gx), gy), dim3(kBwdThreads), args,
-                             2 * kBwdBlockBins * sizeof(float), static_cast<cudaStream_t>(stream)));
+    const size_t smem = kBwdBlockBins * (sizeof(long long) + sizeof(float)) + max_cand * (sizeof(float) + sizeof(int16_t));
+    {
+        hs_status es = ensure_bwd_smem(fn, smem);
+        if (es != HS_OK) return es;
+    }
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(gx), gy), dim3(kBwdThreads), args, smem,
+                             static_cast<cudaStream_t>(stream)));
+    if (grad_w && gy > 1) {
+        const float *part = a.dw_partial;
+        int groups = gy;
+        int64_t n = p->len[0];
+        float *gw = grad_w;
+        void *rargs[] = {&part, &groups, &n, &gw};
+        const unsigned rgrid = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 8 * p->sms));
+        HS_CUDA(cudaLaunchKernel(bwd_dw_reduce_kernel(), dim3(rgrid), dim3(256), rargs, 0,
+                                 static_cast<cudaStream_t>(stream)));
+    }
     return HS_OK;
 }
 
@@ -906,9 +957,7 @@ hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, c
 {
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
-    size_t need = 0;
-    hs_plan_workspace(p, &need);
-    if (need > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;   // plan needs more scratch than the array
+    if (fwd_workspace_bytes(p) > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;   // more scratch than the array
     if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
     const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
     if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;

@@ -108,6 +108,9 @@ struct Bwd1DArgs {
     float *grad_w;
     int64_t n_common;              // N when grad_w is requested
     int32_t block_bins;            // bins per CTA
+    int32_t max_cand;              // shared-memory candidate slots per CTA
+    int32_t group;                 // spectra per CTA (grid.y = ceil(B / group))
+    float *dw_partial;             // [groups][n_common] workspace when grid.y > 1 and grad_w is set
     int64_t blocks_per_spectrum;   // grid.x in per-spectrum mode
     int *err;
 };
@@ -120,5 +123,6 @@ const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel();
 const void *bwd1d_kernel(int form, int dtype, int whitening);
+const void *bwd_dw_reduce_kernel();
 
 }  // namespace hs

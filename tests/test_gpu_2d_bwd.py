@@ -133,6 +133,15 @@ def test_backward_whitening(hs, oracle_lib, dtype):
     bwd_case(hs, oracle_lib, xs, 16, 1, w=w, dtype=dtype)
 
 
+def test_backward_whitening_many_groups(hs, oracle_lib):
+    """More spectra than dL/dw partial groups: each group sums several spectra, then the groups
+    are added in order."""
+    N = 4096
+    w = synth.whitening(N, 9)
+    xs = [synth.spectrum(N, 700 + i, [synth.Pulsar(40.3 + i, 0.05)]) for i in range(20)]
+    bwd_case(hs, oracle_lib, xs, 16, 2, w=w)
+
+
 def test_autograd_topk_loss_matches_fd(hs, oracle_lib):
     """loss = -sum of the top-16 greedy SNRs per spectrum, learnable whitening w (init 1.0):
     the adjoint's dL/dw matches central finite differences (eps = 1e-3) of the FP64 oracle on a

@@ -405,3 +405,31 @@ def test_sector_footprint(oracle_lib):
     s = o.sectors_1d(1, 4, 1 << 20, 32)
     assert max(g, s) <= both <= (1 << 20) // 8
     assert both > 0.95 * (1 << 20) // 8
+
+
+def test_sector_footprint_2d(oracle_lib):
+    """H = 1: the reads are exactly the 3x3 neighbourhoods of the fundamentals, so rows
+    z0 + z - 1 .. z0 + z + 1 are read over columns f_lo - 1 .. f_hi + 1 (closed form)."""
+    o = oracle_lib
+    n_freq, n_rows, z0 = 4096, 21, 10
+    pl = synth.plane(n_freq, n_rows, z0, 3)
+    dom = o.domain_2d(n_freq, n_rows, z0, 1)
+    path = o.greedy_2d(pl, z0, 1, *unit_norm(1))[2]
+    f_lo, f_hi, z_lo, z_hi = dom
+    rows = (z_hi + 1) - (z_lo - 1) + 1
+    per_row = (f_hi + 1) // 8 - (f_lo - 1) // 8 + 1
+    assert o.sectors_2d(n_freq, n_rows, z0, 1, path) == rows * per_row
+    # higher orders only add sectors of the plane; never more than the plane holds
+    path8 = o.greedy_2d(pl, z0, 3, *unit_norm(3))[2]
+    c = o.sectors_2d(n_freq, n_rows, z0, 3, path8)
+    assert 0 < c <= n_rows * n_freq // 8
+
+
+def test_golden_footprints_match_oracle(oracle_lib):
+    """tests/golden/footprints.json (the benchmark's compulsory input bytes) is what the
+    oracle counts for the benchmark spectrum."""
+    gold = json.load(open(os.path.join(GOLD, "footprints.json")))
+    x = synth.long_spectrum()
+    path = oracle_lib.greedy_1d(x, 32, *unit_norm(32))[2]
+    assert gold["long"]["fused"]["sectors"] == oracle_lib.sectors_1d(3, 4, x.size, 32, path=path)
+    assert gold["long"]["simple"]["sectors"] == oracle_lib.sectors_1d(1, 4, x.size, 32)
