@@ -74,7 +74,7 @@ typedef struct {
     int32_t forms;           /* HS_FORM_SIMPLE | HS_FORM_GREEDY (2D: HS_FORM_GREEDY only) */
     int32_t dtype;           /* hs_dtype of the stored input (2D: HS_F32 only) */
     int64_t num_spectra;     /* B >= 1 (1D); 1 for 2D */
-    const int64_t *lengths;  /* host [B]: N_s bins of spectrum s, N_s >= H + 1 (1D) */
+    const int64_t *lengths;  /* host [B]: N_s bins of spectrum s, H + 1 <= N_s < 2^31 - 64 (1D) */
     const int64_t *offsets;  /* host [B] or NULL: element offset of spectrum s in the concatenated
                                 input, each a multiple of 16 bytes / element size; NULL = packed in
                                 order, each start rounded up to 32 elements */
@@ -107,12 +107,14 @@ typedef struct {
  *             staged in shared memory by one bulk copy (TMA) into a ring of `stages` slots of
  *             `stage_kb` KiB; `producers` warps issue the copies (copies of one warp complete in
  *             order, so several producer warps keep several in flight), `threads` consumer
- *             threads run both forms from shared memory (not available with HS_FLAG_WHITENING). */
+ *             threads run both forms from shared memory (not available with HS_FLAG_WHITENING);
+ *   kernel 3: as 0 with two fundamentals per thread (n0 + t and n0 + t + threads), their
+ *             chains interleaved: half the threads, twice the loads in flight per thread. */
 typedef struct {
-    int32_t kernel;          /* 0, 1 or 2 */
-    int32_t threads;         /* fundamentals per CTA tile, multiple of 32: 64..256 (kernels 0/1),
-                                64..512 (kernel 2) */
-    int32_t fund_per_thread; /* 1 */
+    int32_t kernel;          /* 0, 1, 2 or 3 */
+    int32_t threads;         /* threads per CTA (kernel 2: consumer threads), multiple of 32: 64..256
+                                (kernels 0/1/3), 64..512 (kernel 2) */
+    int32_t fund_per_thread; /* 2 for kernel 3, else 1 (a tile is threads x fund_per_thread) */
     int32_t ctas_per_sm;     /* persistent grid = ctas_per_sm x SMs; 0 = kernel 0/1: one CTA per
                                 tile, kernel 2: as many CTAs as fit on an SM */
     int32_t dynamic;         /* kernels 0/1 with a persistent grid: tiles from an atomic counter in

@@ -133,10 +133,11 @@ constexpr int kMaxDynSmem = 232448 - kWinStaticSmem;   // 227 KiB opt-in per CTA
 hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
 {
     if (!t) return HS_ERR_INVALID_ARG;
-    if (t->kernel < 0 || t->kernel > 2) return HS_ERR_INVALID_ARG;
+    if (t->kernel < 0 || t->kernel > 3) return HS_ERR_INVALID_ARG;
     if (t->threads < 64 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
     if (t->threads > (t->kernel == 2 ? 512 : 256)) return HS_ERR_INVALID_ARG;
-    if (t->fund_per_thread != 1) return HS_ERR_UNSUPPORTED;
+    if (t->fund_per_thread != (t->kernel == 3 ? 2 : 1)) return HS_ERR_INVALID_ARG;
+    if (t->kernel == 3 && t->dynamic) return HS_ERR_INVALID_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
     if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
     if (t->prefetch < 0 || t->prefetch > 1) return HS_ERR_INVALID_ARG;
@@ -173,11 +174,10 @@ void make_win_plan(hs_plan p)
 
 hs_tuning default_tuning(const hs_plan p)
 {
-    // one thread per fundamental with read-only gathers, 128-fundamental CTAs: measured on the
-    // 2^23-bin H = 32 spectrum it is the fastest shape for each form alone and ties the window
-    // kernel for the fused pass; HS_FLAG_AUTOTUNE times the alternatives per plan
-    (void)p;
-    return hs_tuning{0, 128, 1, 0, 0, 0, 0, 0, 0};
+    // one thread per fundamental with read-only gathers: measured on the 2^23-bin H = 32
+    // spectrum it is the fastest shape for the fused pass and for each form alone (256-thread
+    // CTAs for FP32, 128 for 16-bit storage); HS_FLAG_AUTOTUNE times the alternatives per plan
+    return hs_tuning{0, p->d.dtype == HS_F32 ? 256 : 128, 1, 0, 0, 0, 0, 0, 0};
 }
 
 hs_status ensure_bwd_smem(const void *fn, size_t bytes)
@@ -440,6 +440,10 @@ hs_status autotune(hs_plan p)
                 if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
             }
         }
+    for (int threads : {64, 128, 256}) {
+        hs_tuning t{3, threads, 2, 0, 0, 0, 0, 0, 0};
+        if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
+    }
     for (int kernel = 0; kernel <= 1; ++kernel)
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
@@ -584,7 +588,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         int64_t pos = 0;
         for (int64_t s = 0; s < B; ++s) {
             const int64_t n = p->len[s];
-            if (n < d.H + 1 || n > (int64_t(1) << 40)) { delete p; return HS_ERR_INVALID_ARG; }
+            if (n < d.H + 1 || n > 0x7fffffffLL - 64) { delete p; return HS_ERR_INVALID_ARG; }
             int64_t off;
             if (d.offsets) {
                 off = d.offsets[s];

@@ -20,7 +20,7 @@ namespace hs {
 template <typename T>
 __device__ __forceinline__ float ld_plain(const void *p, int64_t j)
 {
-    return ld_raw<T>(static_cast<const T *>(p), j);
+    return ld_raw<T, int64_t>(static_cast<const T *>(p), j);
 }
 
 __device__ __forceinline__ uint32_t ld_path(const void *path, int bytes, int64_t i)

@@ -10,32 +10,51 @@ namespace hs {
 // ---------------------------------------------------------------------------------------
 // loads
 // ---------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ float ld_raw(const T *p, int64_t j);
+template <typename T, typename I>
+__device__ __forceinline__ float ld_raw(const T *p, I j);
 
 template <>
-__device__ __forceinline__ float ld_raw<float>(const float *p, int64_t j)
+__device__ __forceinline__ float ld_raw<float, int64_t>(const float *p, int64_t j)
 {
     return __ldg(p + j);
 }
 template <>
-__device__ __forceinline__ float ld_raw<__half>(const __half *p, int64_t j)
+__device__ __forceinline__ float ld_raw<float, uint32_t>(const float *p, uint32_t j)
+{
+    return __ldg(p + j);
+}
+template <typename I>
+__device__ __forceinline__ float ld_half_bits(const __half *p, I j)
 {
     unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + j);
     return __half2float(__ushort_as_half(b));
 }
-template <>
-__device__ __forceinline__ float ld_raw<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t j)
+template <typename I>
+__device__ __forceinline__ float ld_bf16_bits(const __nv_bfloat16 *p, I j)
 {
     unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p) + j);
     return __uint_as_float(static_cast<unsigned int>(b) << 16);
 }
+template <>
+__device__ __forceinline__ float ld_raw<__half, int64_t>(const __half *p, int64_t j) { return ld_half_bits(p, j); }
+template <>
+__device__ __forceinline__ float ld_raw<__half, uint32_t>(const __half *p, uint32_t j) { return ld_half_bits(p, j); }
+template <>
+__device__ __forceinline__ float ld_raw<__nv_bfloat16, int64_t>(const __nv_bfloat16 *p, int64_t j)
+{
+    return ld_bf16_bits(p, j);
+}
+template <>
+__device__ __forceinline__ float ld_raw<__nv_bfloat16, uint32_t>(const __nv_bfloat16 *p, uint32_t j)
+{
+    return ld_bf16_bits(p, j);
+}
 
 // Loaded power x[j]: the stored value, or fl32(w[j] * p[j]) with whitening.
-template <typename T, bool WHITEN>
-__device__ __forceinline__ float ld_x(const T *p, const float *w, int64_t j)
+template <typename T, bool WHITEN, typename I>
+__device__ __forceinline__ float ld_x(const T *p, const float *w, I j)
 {
-    float v = ld_raw<T>(p, j);
+    float v = ld_raw<T, I>(p, j);
     if constexpr (WHITEN) v = __fmul_rn(__ldg(w + j), v);
     return v;
 }
@@ -187,27 +206,31 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
         RunMax ms{0.f, 1}, mg{0.f, 1};
         uint32_t bits = 0;
         if (valid) {
+            // spectra hold fewer than 2^31 bins, so every index of the spectrum fits in 32 bits
+            const uint32_t n32 = static_cast<uint32_t>(n);
+            const float *wv = a.w;
             // ---- order 1 ----
-            const float x0 = ld_x<T, WHITEN>(x, a.w, n);
+            const float x0 = ld_x<T, WHITEN>(x, wv, n32);
             float ss = x0, sg = x0;
-            int d = 0;
+            uint32_t d = 0;
             if (kG && a.mitigation) {
-                const float b = ld_x<T, WHITEN>(x, a.w, n + 1);
+                const float b = ld_x<T, WHITEN>(x, wv, n32 + 1);
                 if (b > x0) { d = 1; sg = b; bits = 1u; }
             }
             if (kS) ms.first(fmaf(ss, nm.rs[0][0], -nm.murs[0][0]));
             if (kG) mg.first(fmaf(sg, nm.rs[1][0], -nm.murs[1][0]));
+            uint32_t hn = n32;            // h n, stepped by n per order
             if constexpr (LOOKAHEAD <= 1) {
                 for (int h = 2; h <= H; ++h) {
-                    const int64_t hn = static_cast<int64_t>(h) * n;
+                    hn += n32;
                     if (kS) {
-                        ss += ld_x<T, WHITEN>(x, a.w, hn);
+                        ss += ld_x<T, WHITEN>(x, wv, hn);
                         ms.step(fmaf(ss, nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
                     }
                     if (kG) {
-                        const int64_t m = hn + d;
-                        const float va = ld_x<T, WHITEN>(x, a.w, m);
-                        const float vb = ld_x<T, WHITEN>(x, a.w, m + 1);
+                        const uint32_t m = hn + d;
+                        const float va = ld_x<T, WHITEN>(x, wv, m);
+                        const float vb = ld_x<T, WHITEN>(x, wv, m + 1);
                         const bool inc = vb > va;
                         sg += inc ? vb : va;
                         d += inc;
@@ -225,15 +248,15 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
                     for (int j = 0; j < G; ++j) {
                         const int h = h0 + j;
                         if (h <= H) {
-                            const int64_t hn = static_cast<int64_t>(h) * n;
-                            if (kS) sv[j] = ld_x<T, WHITEN>(x, a.w, hn);
+                            const uint32_t hnj = hn + static_cast<uint32_t>(j + 1) * n32;
+                            if (kS) sv[j] = ld_x<T, WHITEN>(x, wv, hnj);
                             if (kG) {
 #pragma unroll
-                                for (int i = 0; i <= j + 1; ++i) v[j][i] = ld_x<T, WHITEN>(x, a.w, hn + d + i);
+                                for (int i = 0; i <= j + 1; ++i) v[j][i] = ld_x<T, WHITEN>(x, wv, hnj + d + i);
                             }
                         }
                     }
-                    int r = 0;
+                    uint32_t r = 0;
 #pragma unroll
                     for (int j = 0; j < G; ++j) {
                         const int h = h0 + j;
@@ -246,8 +269,8 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
                                 float va = v[j][0], vb = v[j][1];
 #pragma unroll
                                 for (int i = 1; i <= j; ++i) {
-                                    va = (r == i) ? v[j][i] : va;
-                                    vb = (r == i) ? v[j][i + 1] : vb;
+                                    va = (r == static_cast<uint32_t>(i)) ? v[j][i] : va;
+                                    vb = (r == static_cast<uint32_t>(i)) ? v[j][i + 1] : vb;
                                 }
                                 const bool inc = vb > va;
                                 sg += inc ? vb : va;
@@ -258,6 +281,7 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
                         }
                     }
                     d += r;
+                    hn += static_cast<uint32_t>(G) * n32;
                 }
             }
             const int64_t o = fbase + n;
@@ -291,6 +315,122 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
 }
 
 // ---------------------------------------------------------------------------------------
+// kernel: two fundamentals per thread (n0 + t and n0 + t + blockDim.x), their greedy chains
+// interleaved order by order for instruction-level parallelism; a tile is 2 x blockDim.x
+// fundamentals, so half as many threads cover a spectrum (one wave on the GPU where one
+// fundamental per thread would need a second).
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+__global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
+{
+    __shared__ NormSmem nm;
+    __shared__ unsigned long long red[32];
+    constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
+    constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
+    constexpr int F = 2;
+    const int H = a.H;
+    int loaded_spec = -1;
+    for (int64_t tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
+        const int s = tile_spectrum(a.tile_start, a.B, tile);
+        if (s != loaded_spec) {
+            if (loaded_spec >= 0) __syncthreads();
+            const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
+            if (kS) load_norm(nm, 0, a.s.mu + no, a.s.sigma + no, H);
+            if (kG) load_norm(nm, 1, a.g.mu + no, a.g.sigma + no, H);
+            __syncthreads();
+            loaded_spec = s;
+        }
+        const int64_t fbase = __ldg(a.fund_off + s);
+        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t n0 = (tile - __ldg(a.tile_start + s)) * (F * blockDim.x) + threadIdx.x;
+        const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
+        const float *wv = a.w;
+        uint32_t n[F];
+        bool valid[F];
+        float ss[F], sg[F], bs[F], bg[F];
+        int hs_[F], hg[F];
+        uint32_t d[F], bits[F], hn[F];
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
+            const int64_t ni = n0 + static_cast<int64_t>(i) * blockDim.x;
+            valid[i] = ni < nf;
+            if (a.checked && valid[i] && static_cast<int64_t>(H) * ni + H > __ldg(a.in_len + s) - 1)
+                set_error(a.err, kErrBounds);   // every read lies in [0, H n + H]
+            n[i] = valid[i] ? static_cast<uint32_t>(ni) : 0u;   // invalid lanes read bin 0 (harmless)
+            const float x0 = ld_x<T, WHITEN>(x, wv, n[i]);
+            ss[i] = x0;
+            sg[i] = x0;
+            d[i] = 0;
+            bits[i] = 0;
+            if (kG && a.mitigation) {
+                const float b = ld_x<T, WHITEN>(x, wv, n[i] + 1);
+                if (b > x0) { d[i] = 1; sg[i] = b; bits[i] = 1u; }
+            }
+            bs[i] = fmaf(ss[i], nm.rs[0][0], -nm.murs[0][0]);
+            bg[i] = fmaf(sg[i], nm.rs[1][0], -nm.murs[1][0]);
+            hs_[i] = 1;
+            hg[i] = 1;
+            hn[i] = n[i];
+        }
+        for (int h = 2; h <= H; ++h) {
+            const float rs0 = nm.rs[0][h - 1], mr0 = nm.murs[0][h - 1];
+            const float rs1 = nm.rs[1][h - 1], mr1 = nm.murs[1][h - 1];
+            float xs[F], va[F], vb[F];
+#pragma unroll
+            for (int i = 0; i < F; ++i) {       // all loads of this order first
+                hn[i] += n[i];
+                if (kS) xs[i] = ld_x<T, WHITEN>(x, wv, hn[i]);
+                if (kG) {
+                    va[i] = ld_x<T, WHITEN>(x, wv, hn[i] + d[i]);
+                    vb[i] = ld_x<T, WHITEN>(x, wv, hn[i] + d[i] + 1);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                if (kS) {
+                    ss[i] += xs[i];
+                    const float v = fmaf(ss[i], rs0, -mr0);
+                    if (v > bs[i]) { bs[i] = v; hs_[i] = h; }
+                }
+                if (kG) {
+                    const bool inc = vb[i] > va[i];
+                    sg[i] += inc ? vb[i] : va[i];
+                    d[i] += inc;
+                    bits[i] |= static_cast<uint32_t>(inc) << (h - 1);
+                    const float v = fmaf(sg[i], rs1, -mr1);
+                    if (v > bg[i]) { bg[i] = v; hg[i] = h; }
+                }
+            }
+        }
+        unsigned long long ks = 0ull, kg = 0ull;
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
+            if (!valid[i]) continue;
+            const int64_t o = fbase + n[i];
+            if (kS) {
+                a.s.snr[o] = bs[i];
+                a.s.best_h[o] = static_cast<uint8_t>(hs_[i]);
+                const unsigned long long kk = argmax_key(bs[i], n[i]);
+                ks = kk > ks ? kk : ks;
+            }
+            if (kG) {
+                a.g.snr[o] = bg[i];
+                a.g.best_h[o] = static_cast<uint8_t>(hg[i]);
+                if (a.g.path) store_path(a.g.path, a.path_bytes, o, bits[i]);
+                const unsigned long long kk = argmax_key(bg[i], n[i]);
+                kg = kk > kg ? kk : kg;
+            }
+        }
+        if (kS && a.s.argmax) block_argmax(ks, a.s.argmax + s, red);
+        if (kG && a.g.argmax) {
+            if (kS && a.s.argmax) __syncthreads();
+            block_argmax(kg, a.g.argmax + s, red);
+        }
+        if (tile + gridDim.x < a.total_tiles) __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // dispatch for one stored type
 // ---------------------------------------------------------------------------------------
 template <typename T, int FORMS, bool WHITEN>
@@ -299,6 +439,7 @@ static const void *fwd1d_kernel_ptr(int kernel)
     switch (kernel) {
     case 0: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 1>);
     case 1: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 4>);
+    case 3: return reinterpret_cast<const void *>(&k_fwd1d_x2<T, FORMS, WHITEN>);
     default: return nullptr;
     }
 }

@@ -132,13 +132,15 @@ def test_tuning_validation(hs):
     p = plan(hs, H=8, forms=3, lengths=[10000])
     t = p.tuning
     assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
-    assert t.kernel == 0 and t.threads == 128
+    assert t.kernel == 0 and t.threads == 256
+    assert plan(hs, H=8, forms=3, lengths=[10000], dtype=hs.F16).tuning.threads == 128
     p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
     assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1,
                                       stages=0, stage_kb=0, prefetch=0, producers=0)
     with pytest.raises(hs.HSError):      # L2 prefetch belongs to the window kernel
         p.tuning = dict(kernel=0, threads=128, prefetch=1)
     p.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=24, prefetch=1, producers=2)
+    p.tuning = dict(kernel=3, threads=128, fund_per_thread=2)
     p.tuning = dict(kernel=2, threads=256, stages=2, stage_kb=96, producers=1)
     big = plan(hs, H=32, forms=3, lengths=[100000])
     with pytest.raises(hs.HSError):      # order-32 window of a 256-wide tile needs ~32 KiB
@@ -162,7 +164,9 @@ def test_tuning_validation(hs):
                 dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=0, dynamic=1),
                 dict(kernel=2, threads=128, stages=1, stage_kb=48, producers=1),
                 dict(kernel=2, threads=128, stages=17, stage_kb=8, producers=1),
-                dict(kernel=2, threads=128, stages=4, stage_kb=8, producers=0)):
+                dict(kernel=2, threads=128, stages=4, stage_kb=8, producers=0),
+                dict(kernel=3, threads=128, fund_per_thread=1),
+                dict(kernel=0, threads=128, fund_per_thread=2)):
         with pytest.raises(hs.HSError):
             p.tuning = bad
 

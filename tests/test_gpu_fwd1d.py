@@ -91,7 +91,9 @@ TUNINGS = [dict(kernel=0, threads=256),
            dict(kernel=2, threads=64, stages=4, stage_kb=9, producers=2, ctas_per_sm=3),
            dict(kernel=2, threads=256, stages=6, stage_kb=33, producers=6, ctas_per_sm=1, prefetch=1),
            dict(kernel=2, threads=96, stages=3, stage_kb=13, producers=1, ctas_per_sm=2),
-           dict(kernel=2, threads=448, stages=3, stage_kb=57, producers=3)]
+           dict(kernel=2, threads=448, stages=3, stage_kb=57, producers=3),
+           dict(kernel=3, threads=128, fund_per_thread=2),
+           dict(kernel=3, threads=64, fund_per_thread=2, ctas_per_sm=5)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -101,13 +103,13 @@ def test_fused_f32_shapes(hs, oracle_lib, H, tuning):
     run_case(hs, oracle_lib, [x], H, tuning=tuning)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("forms", [1, 2, 3])
 @pytest.mark.parametrize("mitigation", [True, False])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
 def test_forms_dtypes(hs, oracle_lib, forms, mitigation, dtype, kernel):
     x = synth.single_pulse_spectrum()
-    t = TUNINGS[5] if kernel == 2 else TUNINGS[1]
+    t = {1: TUNINGS[1], 2: TUNINGS[5], 3: TUNINGS[10]}[kernel]
     run_case(hs, oracle_lib, [x], 32, forms=forms, dtype=dtype, mitigation=mitigation, tuning=t)
 
 
@@ -122,14 +124,14 @@ def test_window_unaligned_tails(hs, oracle_lib, dtype, n):
         run_case(hs, oracle_lib, xs, 32, dtype=dtype, tuning=t)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 3])
 def test_whitening(hs, oracle_lib, kernel):
     N = 65536
     w = synth.whitening(N, 5)
     xs = [synth.spectrum(N, 50 + i, [synth.Pulsar(300.4 + 17 * i, 0.07)]) for i in range(3)]
     for dtype in (0, 1, 2):
         run_case(hs, oracle_lib, xs, 16, w=w, dtype=dtype,
-                 tuning=dict(kernel=kernel, threads=256))
+                 tuning=dict(kernel=kernel, threads=256, fund_per_thread=2 if kernel == 3 else 1))
 
 
 def test_small_and_degenerate_lengths(hs, oracle_lib):
