@@ -47,17 +47,26 @@ METRIC = "bins×harmonics/s and HBM GB/s (% of peak), greedy vs simple HS at H=3
 UNIT = "bins*harmonics/s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "footprints.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f32.cu", "hs_fwd1d_f16.cu", "hs_fwd1d_bf16.cu",
-                  "hs_fwd2d.cu", "hs_bwd1d.cu", "hs_internal.cuh", "hs_api.cu"]
+# sources of the kernel each workload times (the ncu counters under profiles/ hold for them only)
+KERNEL_SOURCES = {
+    "long": ["hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "long16": ["hs_fwd1d.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
+    "longbf16": ["hs_fwd1d.cuh", "hs_fwd1d_bf16.cu", "hs_internal.cuh"],
+    "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
+    "plane": ["hs_fwd2d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
+}
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def kernel_hash() -> str:
+def kernel_hash(wl: str) -> str:
+    """Hash of the sources of the kernel a workload times."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES.get(wl, []):
         p = os.path.join(ROOT, "paper_2202_12817_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -257,11 +266,13 @@ def time_steps(torch, step, K, stream, flush=None):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def roofline(alg_bytes, ms, peak, peak_kind, wl, how):
+def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
+    """roofline entry; `traffic` = DRAM bytes per launch from the committed ncu capture of this
+    workload, reported only while the kernel's sources and launch shape are those captured."""
     achieved = alg_bytes / (ms / 1e3) / 1e9
     prof = load_json(PROFILE_TRAFFIC) or {}
     pk = prof.get(wl) or {}
-    fresh = pk.get("kernel_hash") == kernel_hash()
+    fresh = pk.get("kernel_hash") == kernel_hash(wl) and pk.get("tuning") == tuning
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": pk.get("dram_bytes_per_launch") if fresh else None,
             "algorithmic_bytes": int(alg_bytes), "bytes_basis": how, "peak_kind": peak_kind,
@@ -366,7 +377,7 @@ def wl_long(args, hs, torch, dev, world, dist):
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "flushed before every timed step (write of max(2 x L2, 256 MiB))",
                    "tuning": plan.tuning.as_dict()},
-        "roofline": roofline(alg, ms, peak, peak_kind, wl, how),
+        "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "per_form": per_form,
         "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(x.numel() * x.element_size()),
@@ -421,7 +432,7 @@ def wl_batch(args, hs, torch, dev, world, dist):
                                "H=16, 5% with a pulsar, one persistent launch from a CUDA graph",
                    "bins": int(sum(b.lengths)), "H": H, "fundamentals": int(nf), "spectra": len(b.lengths),
                    "l2": "inputs larger than L2 (no flush)", "tuning": plan.tuning.as_dict()},
-        "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how),
+        "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how, plan.tuning.as_dict()),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }
     i0 = int(np.argmax(b.lengths))
@@ -470,7 +481,7 @@ def wl_plane(args, hs, torch, dev, world, dist):
         "config": {"workload": "2D greedy over an f-fdot plane 201 x 2^21 (FP32), H=8, 8 drifting signals",
                    "fundamentals": int(nfund), "H": H, "domain": list(plan.domain),
                    "l2": "input larger than L2 (no flush)"},
-        "roofline": roofline(alg, ms, peak, peak_kind, "plane", how),
+        "roofline": roofline(alg, ms, peak, peak_kind, "plane", how, None),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }
     host_plane = pl.cpu().numpy()
@@ -534,7 +545,8 @@ def wl_grad(args, hs, torch, dev, world, dist):
                    "fwd_ms": round(f_ms, 4), "bwd_ms": round(b_ms, 4), "l2": "inputs larger than L2 (no flush)",
                    "tuning": plan.tuning.as_dict()},
         "roofline": roofline(fwd_bytes + bwd_bytes, ms, peak, peak_kind, "grad",
-                             "fwd: oracle sector fraction x input + w + outputs; bwd: input + forward outputs + dL/dw"),
+                             "fwd: oracle sector fraction x input + w + outputs; bwd: input + forward outputs + dL/dw",
+                             plan.tuning.as_dict()),
         "gpu_launches": 2 * steps, "wall_s_timed_region": round(wall, 3),
     }
     xs_host = p[:N].cpu().numpy()
