@@ -109,9 +109,10 @@ typedef struct {
  *             order, so several producer warps keep several in flight), `threads` consumer
  *             threads run both forms from shared memory (not available with HS_FLAG_WHITENING);
  *   kernel 3: as 0 with two fundamentals per thread (n0 + t and n0 + t + threads), their
- *             chains interleaved: half the threads, twice the loads in flight per thread. */
+ *             chains interleaved: half the threads, twice the loads in flight per thread;
+ *   kernels 4, 5: as 1 with look-ahead over 2 or 3 orders. */
 typedef struct {
-    int32_t kernel;          /* 0, 1, 2 or 3 */
+    int32_t kernel;          /* 0..5 */
     int32_t threads;         /* threads per CTA (kernel 2: consumer threads), multiple of 32: 64..256
                                 (kernels 0/1/3), 64..512 (kernel 2) */
     int32_t fund_per_thread; /* 2 for kernel 3, else 1 (a tile is threads x fund_per_thread) */

@@ -133,9 +133,10 @@ constexpr int kMaxDynSmem = 232448 - kWinStaticSmem;   // 227 KiB opt-in per CTA
 hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
 {
     if (!t) return HS_ERR_INVALID_ARG;
-    if (t->kernel < 0 || t->kernel > 3) return HS_ERR_INVALID_ARG;
+    if (t->kernel < 0 || t->kernel > 5) return HS_ERR_INVALID_ARG;
     if (t->threads < 64 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
     if (t->threads > (t->kernel == 2 ? 512 : 256)) return HS_ERR_INVALID_ARG;
+    if (t->kernel == 2 && (p->d.flags & HS_FLAG_WHITENING)) return HS_ERR_UNSUPPORTED;
     if (t->fund_per_thread != (t->kernel == 3 ? 2 : 1)) return HS_ERR_INVALID_ARG;
     if (t->kernel == 3 && t->dynamic) return HS_ERR_INVALID_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
@@ -444,7 +445,7 @@ hs_status autotune(hs_plan p)
         hs_tuning t{3, threads, 2, 0, 0, 0, 0, 0, 0};
         if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
     }
-    for (int kernel = 0; kernel <= 1; ++kernel)
+    for (int kernel : {0, 1, 4, 5})
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
                 hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, 0, 0};

@@ -433,6 +433,8 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
 // ---------------------------------------------------------------------------------------
 // dispatch for one stored type
 // ---------------------------------------------------------------------------------------
+// kernel ids: 0 = direct gather; 1 = look-ahead over 4 orders; 3 = two fundamentals per thread;
+// 4, 5 = look-ahead over 2, 3 orders
 template <typename T, int FORMS, bool WHITEN>
 static const void *fwd1d_kernel_ptr(int kernel)
 {
@@ -440,6 +442,8 @@ static const void *fwd1d_kernel_ptr(int kernel)
     case 0: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 1>);
     case 1: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 4>);
     case 3: return reinterpret_cast<const void *>(&k_fwd1d_x2<T, FORMS, WHITEN>);
+    case 4: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 2>);
+    case 5: return reinterpret_cast<const void *>(&k_fwd1d<T, FORMS, WHITEN, 3>);
     default: return nullptr;
     }
 }

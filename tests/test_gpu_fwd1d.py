@@ -93,7 +93,9 @@ TUNINGS = [dict(kernel=0, threads=256),
            dict(kernel=2, threads=96, stages=3, stage_kb=13, producers=1, ctas_per_sm=2),
            dict(kernel=2, threads=448, stages=3, stage_kb=57, producers=3),
            dict(kernel=3, threads=128, fund_per_thread=2),
-           dict(kernel=3, threads=64, fund_per_thread=2, ctas_per_sm=5)]
+           dict(kernel=3, threads=64, fund_per_thread=2, ctas_per_sm=5),
+           dict(kernel=4, threads=128),
+           dict(kernel=5, threads=256, ctas_per_sm=3, dynamic=1)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
