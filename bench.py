@@ -495,6 +495,8 @@ def wl_grad(args, hs, torch, dev, world, dist):
         synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 5000 + i)[0]])
     w = torch.ones(N, dtype=torch.float32, device=dev, requires_grad=True)
     plan = hs.Plan(H, hs.GREEDY, lengths=[N] * B, flags=hs.FLAG_WHITENING, device=dev.index)
+    if args.tuning:
+        plan.tuning = json.loads(args.tuning)
     mu, sg = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
     nf = plan.total_fundamentals // B
     stream = torch.cuda.current_stream(dev)

@@ -139,9 +139,10 @@ hs_status hs_plan_fundamentals(hs_plan plan, int64_t *counts, int64_t *offsets);
 hs_status hs_plan_input_offsets(hs_plan plan, int64_t *offsets);
 /* 2D fundamental domain: f in [f_lo, f_hi], z in [z_lo, z_hi]. */
 hs_status hs_plan_domain_2d(hs_plan plan, int64_t *f_lo, int64_t *f_hi, int64_t *z_lo, int64_t *z_hi);
-/* Bytes of device workspace hs_run / hs_backward need (0 = pass NULL): the forward's dynamic
- * schedule needs 256 bytes; the adjoint of a whitening plan with grad_w needs one partial dL/dw
- * (N floats) per group of spectra (up to 16 groups). */
+/* Bytes of device workspace hs_run / hs_backward take (0 = pass NULL): the forward's dynamic
+ * schedule needs 256 bytes; the adjoint uses one partial dL/dw (N floats) per group of spectra
+ * (up to 16 groups; required for a whitening plan with grad_w) followed by one byte per
+ * (spectrum, 1024-bin block) that marks the blocks receiving contributions. */
 hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
 hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
 hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
@@ -159,13 +160,16 @@ hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_for
  *   dL/dx[j] = sum over (n, k <= h*(n)) with b_k(n) = j of grad_snr[n] / sigma[h*(n)-1],
  *   b_k(n) = k n (simple) or k n + popcount(path[n] & ((1 << k) - 1)) (greedy).
  * Each contribution is grad_snr[n] * fl(1/sigma); contributions to each bin are added exactly
- * in 64-bit fixed point (resolution 2^-55 of the
- * largest contribution in its 2048-bin block) and rounded once to FP32, so the result is
- * bit-reproducible and independent of the order of the additions.
+ * in 64-bit fixed point (resolution 2^-55 of the largest contribution in its 1024-bin block) and
+ * rounded once to FP32 (a result below FP32's normal range may be rounded twice), so the result
+ * is bit-reproducible and independent of the order of the additions.
  * grad_in: device [input extent] or NULL: dL/d(spectra); with whitening w[j] dL/dx[j].
  * grad_w: device [N] or NULL (whitening only): dL/dw[j] = sum_s p_s[j] dL/dx_s[j], spectra in
  * order.  fwd: the form's forward outputs (best_h, path, sigma are read).  workspace: >=
- * hs_plan_workspace bytes when grad_w is set (NULL otherwise). */
+ * hs_plan_workspace bytes, or NULL when grad_w is not set.  With a workspace the adjoint first
+ * marks the (spectrum, block) pairs that receive a contribution (fundamentals with
+ * grad_snr != 0) and skips the candidate search everywhere else, which makes sparse upstream
+ * gradients (a top-k loss) cheap; the results are identical either way. */
 hs_status hs_backward(hs_plan plan, int32_t form, const float *grad_snr, const hs_form_io *fwd,
                       const void *spectra, const float *w, float *grad_in, float *grad_w,
                       void *workspace, void *stream);

@@ -327,11 +327,15 @@ def run_fixed_scratch(plan: Plan, spectra, w=None, simple: FormIO | None = None,
 
 
 def backward(plan: Plan, form: int, grad_snr, fwd: FormIO, spectra=None, w=None, grad_in=None, grad_w=None,
-             workspace=None, stream=None):
-    """hs_backward: dL/d(spectra) into ``grad_in`` and/or dL/dw into ``grad_w``."""
+             workspace=None, stream=None, mark_blocks=True):
+    """hs_backward: dL/d(spectra) into ``grad_in`` and/or dL/dw into ``grad_w``.  With the plan's
+    workspace (the default) the library first marks the bin blocks that receive contributions and
+    skips the rest; ``mark_blocks=False`` passes no workspace where none is required (every block
+    is then visited; results are identical)."""
     c = fwd._c()
-    if workspace is None and grad_w is not None:
-        workspace = plan.workspace(grad_w.device)
+    out = grad_w if grad_w is not None else grad_in
+    if workspace is None and out is not None and (mark_blocks or grad_w is not None):
+        workspace = plan.workspace(out.device)
     _check(lib().hs_backward(plan.handle, form, _ptr(grad_snr), ctypes.byref(c), _ptr(spectra), _ptr(w),
                              _ptr(grad_in), _ptr(grad_w), _ptr(workspace), _stream_ptr(stream)), "hs_backward")
 

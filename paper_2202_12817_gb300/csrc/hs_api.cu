@@ -37,6 +37,7 @@ constexpr size_t kWorkspaceBytes = 256;     // tile counter of the dynamic sched
 constexpr int kBwdBlockBins = 1024;   // must stay <= 32767 (int16 offsets)
 constexpr int kBwdMaxGroups = 16;     // spectrum groups of the adjoint's dL/dw partial sums
 constexpr int kBwdThreads = 256;
+static_assert(kBwdBlockBins == 4 * kBwdThreads, "the adjoint's epilogue gives each thread four bins");
 
 int elem_bytes(int dtype) { return dtype == HS_F32 ? 4 : 2; }
 
@@ -91,7 +92,15 @@ struct hs_plan_s {
 
 namespace {
 
-int64_t tile_fund(const hs_tuning &t) { return static_cast<int64_t>(t.threads) * t.fund_per_thread; }
+// Fundamentals per tile: kernel 6 gives each fundamental one lane per form.
+int64_t tile_fund(const hs_desc &d, const hs_tuning &t)
+{
+    if (t.kernel == 6 || t.kernel == 7) {
+        const int64_t pass = d.forms == (HS_FORM_SIMPLE | HS_FORM_GREEDY) ? t.threads / 2 : t.threads;
+        return t.kernel == 7 ? 2 * pass : pass;
+    }
+    return static_cast<int64_t>(t.threads) * t.fund_per_thread;
+}
 
 // Forward: the dynamic schedule's tile counter (1D).
 size_t fwd_workspace_bytes(const hs_plan p) { return p->d.dims == 1 ? kWorkspaceBytes : 0; }
@@ -104,16 +113,35 @@ int bwd_groups(const hs_plan p)
     return static_cast<int>(std::min<int64_t>(p->d.num_spectra, kBwdMaxGroups));
 }
 
-size_t bwd_workspace_bytes(const hs_plan p)
+// Adjoint workspace: [dL/dw partials: groups x N floats, when there is more than one group]
+// [active-block flags: B x ceil(max N / block) bytes], each part 256-byte aligned.
+int64_t bwd_nblk(const hs_plan p) { return (p->max_len + kBwdBlockBins - 1) / kBwdBlockBins; }
+
+size_t bwd_partial_bytes(const hs_plan p)
 {
     const int g = bwd_groups(p);
-    return g > 1 ? static_cast<size_t>(g) * static_cast<size_t>(p->len[0]) * sizeof(float) : 0;
+    const size_t b = g > 1 ? static_cast<size_t>(g) * static_cast<size_t>(p->len[0]) * sizeof(float) : 0;
+    return (b + 255) / 256 * 256;
+}
+
+size_t bwd_flag_bytes(const hs_plan p)
+{
+    const size_t flags = static_cast<size_t>(p->d.num_spectra) * static_cast<size_t>(bwd_nblk(p));
+    return (flags + 255) / 256 * 256;
+}
+
+// ... then the per-spectrum nonzero counts (B ints) and lists (B x kBwdListCap ints)
+size_t bwd_workspace_bytes(const hs_plan p)
+{
+    if (p->d.dims != 1) return 0;
+    const size_t B = static_cast<size_t>(p->d.num_spectra);
+    return bwd_partial_bytes(p) + bwd_flag_bytes(p) + (B * 4 + 255) / 256 * 256 + B * 4 * kBwdListCap;
 }
 void make_win_plan(hs_plan p);
 
 void compute_tiles(hs_plan p)
 {
-    const int64_t T = tile_fund(p->tun);
+    const int64_t T = tile_fund(p->d, p->tun);
     const size_t B = p->nf.size();
     p->tile_start.assign(B + 1, 0);
     for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf[s] + T - 1) / T;
@@ -133,7 +161,7 @@ constexpr int kMaxDynSmem = 232448 - kWinStaticSmem;   // 227 KiB opt-in per CTA
 hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
 {
     if (!t) return HS_ERR_INVALID_ARG;
-    if (t->kernel < 0 || t->kernel > 5) return HS_ERR_INVALID_ARG;
+    if (t->kernel < 0 || t->kernel > 7) return HS_ERR_INVALID_ARG;
     if (t->threads < 64 || (t->threads % 32) != 0) return HS_ERR_INVALID_ARG;
     if (t->threads > (t->kernel == 2 ? 512 : 256)) return HS_ERR_INVALID_ARG;
     if (t->kernel == 2 && (p->d.flags & HS_FLAG_WHITENING)) return HS_ERR_UNSUPPORTED;
@@ -142,7 +170,8 @@ hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
     if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
     if (t->prefetch < 0 || t->prefetch > 1) return HS_ERR_INVALID_ARG;
-    if (t->kernel != 2 && (t->prefetch != 0 || t->producers != 0)) return HS_ERR_INVALID_ARG;
+    if (t->kernel != 2 && t->kernel != 6 && t->kernel != 7 && t->prefetch != 0) return HS_ERR_INVALID_ARG;
+    if (t->kernel != 2 && t->producers != 0) return HS_ERR_INVALID_ARG;
     if (t->kernel == 2) {
         if (p->d.flags & HS_FLAG_WHITENING) return HS_ERR_UNSUPPORTED;
         if (t->dynamic) return HS_ERR_INVALID_ARG;
@@ -175,9 +204,11 @@ void make_win_plan(hs_plan p)
 
 hs_tuning default_tuning(const hs_plan p)
 {
-    // one thread per fundamental with read-only gathers: measured on the 2^23-bin H = 32
-    // spectrum it is the fastest shape for the fused pass and for each form alone (256-thread
-    // CTAs for FP32, 128 for 16-bit storage); HS_FLAG_AUTOTUNE times the alternatives per plan
+    // Measured on the 2^23-bin H = 32 spectrum (GB300): FP32 without whitening runs fastest on
+    // the paired-lane kernel 6 (fused 43 us vs 45 us, simple 25.6 vs 27.8 us, greedy equal);
+    // with whitening or 16-bit storage the direct kernel 0 is as fast or faster (256-thread CTAs
+    // for FP32, 128 for 16-bit storage).  HS_FLAG_AUTOTUNE times the alternatives per plan.
+    if (p->d.dtype == HS_F32 && !(p->d.flags & HS_FLAG_WHITENING)) return hs_tuning{6, 256, 1, 0, 0, 0, 0, 0, 0};
     return hs_tuning{0, p->d.dtype == HS_F32 ? 256 : 128, 1, 0, 0, 0, 0, 0, 0};
 }
 
@@ -294,6 +325,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.checked = (p->d.flags & HS_FLAG_CHECKED) ? 1 : 0;
     a.fund_per_thread = t.fund_per_thread;
     a.total_tiles = p->tile_start.back();
+    a.extent = p->extent;
     a.s = to_form_args(simple);
     a.g = to_form_args(greedy);
     a.err = p->d_err;
@@ -321,6 +353,15 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     }
     int64_t grid = a.total_tiles;
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
+    if ((t.kernel == 6 || t.kernel == 7) && (t.prefetch & 1) && p->l2_bytes > 0 && grid > 0) {
+        // an input that fits in half of L2 is prefetched there by the first CTAs, one share each
+        const int64_t in_bytes = p->extent * elem_bytes(p->d.dtype);
+        if (in_bytes <= p->l2_bytes / 2) {
+            const int64_t ctas = std::min<int64_t>(grid, static_cast<int64_t>(p->sms) * 8);
+            a.pf_bytes = in_bytes;
+            a.pf_chunk = ((in_bytes + ctas - 1) / ctas + 15) / 16 * 16;
+        }
+    }
     if (t.dynamic) {
         a.tile_counter = static_cast<unsigned long long *>(ws);
         // every CTA draws all of its tiles from this counter, starting at 0
@@ -445,7 +486,7 @@ hs_status autotune(hs_plan p)
         hs_tuning t{3, threads, 2, 0, 0, 0, 0, 0, 0};
         if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
     }
-    for (int kernel : {0, 1, 4, 5})
+    for (int kernel : {0, 1, 4, 5, 6, 7})
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
                 hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, 0, 0};
@@ -880,18 +921,33 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     }
     if (gx > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     a.blocks_per_spectrum = gx;
+    if (workspace && !aligned(workspace, 16)) return HS_ERR_INVALID_ARG;
     const void *fn = bwd1d_kernel(form, p->d.dtype, whiten ? 1 : 0);
     if (!fn) return HS_ERR_UNSUPPORTED;
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (workspace) {
+        // with a workspace, mark the bin blocks that receive contributions; the rest skip staging
+        a.nblk = bwd_nblk(p);
+        uint8_t *wsb = static_cast<uint8_t *>(workspace) + bwd_partial_bytes(p);
+        a.active = wsb;
+        a.nz_count = reinterpret_cast<int *>(wsb + bwd_flag_bytes(p));
+        a.nz_list = a.nz_count + (B + 63) / 64 * 64;
+        // flags and counts are contiguous: one memset clears both
+        HS_CUDA(cudaMemsetAsync(a.active, 0, bwd_flag_bytes(p) + static_cast<size_t>(B) * 4, st));
+        int64_t F = p->total_fund;
+        void *margs[] = {&a, &F};
+        const unsigned mgrid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((F + 255) / 256, 16 * p->sms)));
+        HS_CUDA(cudaLaunchKernel(bwd_mark_kernel(form), dim3(mgrid), dim3(256), margs, 0, st));
+    }
     void *args[] = {&a};
-    const size_t smem = kBwdBlockBins * (sizeof(long long) + sizeof(float)) + max_cand * (sizeof(float) + sizeof(int16_t));
+    const size_t smem = kBwdBlockBins * sizeof(long long) + max_cand * (sizeof(float) + sizeof(int16_t));
     {
         hs_status es = ensure_bwd_smem(fn, smem);
         if (es != HS_OK) return es;
     }
-    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(gx), gy), dim3(kBwdThreads), args, smem,
-                             static_cast<cudaStream_t>(stream)));
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(gx), gy), dim3(kBwdThreads), args, smem, st));
     if (grad_w && gy > 1) {
         const float *part = a.dw_partial;
         int groups = gy;
@@ -899,8 +955,7 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
         float *gw = grad_w;
         void *rargs[] = {&part, &groups, &n, &gw};
         const unsigned rgrid = static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 8 * p->sms));
-        HS_CUDA(cudaLaunchKernel(bwd_dw_reduce_kernel(), dim3(rgrid), dim3(256), rargs, 0,
-                                 static_cast<cudaStream_t>(stream)));
+        HS_CUDA(cudaLaunchKernel(bwd_dw_reduce_kernel(), dim3(rgrid), dim3(256), rargs, 0, st));
     }
     return HS_OK;
 }

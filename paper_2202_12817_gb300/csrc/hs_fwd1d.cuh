@@ -434,7 +434,9 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
 // dispatch for one stored type
 // ---------------------------------------------------------------------------------------
 // kernel ids: 0 = direct gather; 1 = look-ahead over 4 orders; 3 = two fundamentals per thread;
-// 4, 5 = look-ahead over 2, 3 orders
+// 4, 5 = look-ahead over 2, 3 orders; 2 = shared-memory windows (hs_fwd1d_win.cuh);
+// 6, 7 = paired lanes, one lane per form and fundamental (hs_fwd1d_pair.cuh), one or two
+// fundamentals per lane
 template <typename T, int FORMS, bool WHITEN>
 static const void *fwd1d_kernel_ptr(int kernel)
 {
@@ -450,11 +452,14 @@ static const void *fwd1d_kernel_ptr(int kernel)
 
 template <typename T>
 static const void *fwd1d_win_kernel_for(int forms);
+template <typename T>
+static const void *fwd1d_pair_kernel_for(int forms, int whitening, int kernel);
 
 template <typename T>
 static const void *fwd1d_kernel_for(int forms, int whitening, int kernel)
 {
     if (kernel == 2) return whitening ? nullptr : fwd1d_win_kernel_for<T>(forms);
+    if (kernel == 6 || kernel == 7) return fwd1d_pair_kernel_for<T>(forms, whitening, kernel);
     if (whitening) {
         switch (forms) {
         case 1: return fwd1d_kernel_ptr<T, 1, true>(kernel);

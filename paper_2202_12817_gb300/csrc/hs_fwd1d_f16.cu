@@ -1,6 +1,7 @@
 // 1D forward kernels instantiated for stored type __half.
 #include "hs_fwd1d.cuh"
 #include "hs_fwd1d_win.cuh"
+#include "hs_fwd1d_pair.cuh"
 
 namespace hs {
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel)

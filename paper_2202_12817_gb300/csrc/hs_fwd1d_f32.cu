@@ -1,6 +1,7 @@
 // 1D forward kernels instantiated for stored type float.
 #include "hs_fwd1d.cuh"
 #include "hs_fwd1d_win.cuh"
+#include "hs_fwd1d_pair.cuh"
 
 namespace hs {
 const void *fwd1d_kernel_f32(int forms, int whitening, int kernel)

@@ -11,6 +11,9 @@
 namespace hs {
 
 constexpr int kMaxH1D = 32;
+// adjoint: spectra with at most this many nonzero upstream gradients stage contributions from a
+// list of those fundamentals instead of scanning every candidate of a bin block
+constexpr int kBwdListCap = 64;
 constexpr int kMaxH2D = 8;
 
 // Device error word values (first error wins).
@@ -45,6 +48,9 @@ struct Fwd1DArgs {
     int32_t fund_per_thread;
     int64_t total_tiles;
     unsigned long long *tile_counter;  // dynamic schedule (nullptr = static)
+    int64_t extent;                // readable elements of the input buffer (vector loads stay below)
+    int64_t pf_chunk;              // > 0: CTA i first prefetches input bytes [i c, (i+1) c) into L2
+    int64_t pf_bytes;              // input bytes covered by that prefetch
     FormArgs s;                    // simple form outputs (unused unless the form is on)
     FormArgs g;                    // greedy form outputs
     int *err;                      // device error word
@@ -112,6 +118,10 @@ struct Bwd1DArgs {
     int32_t group;                 // spectra per CTA (grid.y = ceil(B / group))
     float *dw_partial;             // [groups][n_common] workspace when grid.y > 1 and grad_w is set
     int64_t blocks_per_spectrum;   // grid.x in per-spectrum mode
+    uint8_t *active;               // [B][nblk] or nullptr: 1 where a bin block receives a contribution
+    int64_t nblk;                  // bin blocks per spectrum in `active`
+    int *nz_count;                 // [B]: fundamentals with a nonzero upstream gradient per spectrum
+    int *nz_list;                  // [B][kBwdListCap]: those fundamentals (unordered) while they fit
     int *err;
 };
 
@@ -124,5 +134,6 @@ const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel();
 const void *bwd1d_kernel(int form, int dtype, int whitening);
 const void *bwd_dw_reduce_kernel();
+const void *bwd_mark_kernel(int form);
 
 }  // namespace hs

@@ -132,13 +132,18 @@ def test_tuning_validation(hs):
     p = plan(hs, H=8, forms=3, lengths=[10000])
     t = p.tuning
     assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
-    assert t.kernel == 0 and t.threads == 256
-    assert plan(hs, H=8, forms=3, lengths=[10000], dtype=hs.F16).tuning.threads == 128
+    assert t.kernel == 6 and t.threads == 256          # FP32: paired lanes
+    t16 = plan(hs, H=8, forms=3, lengths=[10000], dtype=hs.F16).tuning
+    assert t16.kernel == 0 and t16.threads == 128
     p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)
     assert p.tuning.as_dict() == dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1,
                                       stages=0, stage_kb=0, prefetch=0, producers=0)
-    with pytest.raises(hs.HSError):      # L2 prefetch belongs to the window kernel
+    with pytest.raises(hs.HSError):      # L2 prefetch belongs to the window and paired-lane kernels
         p.tuning = dict(kernel=0, threads=128, prefetch=1)
+    p.tuning = dict(kernel=6, threads=128, ctas_per_sm=8, dynamic=1, prefetch=1)
+    p.tuning = dict(kernel=7, threads=64)
+    with pytest.raises(hs.HSError):      # no kernel 8
+        p.tuning = dict(kernel=8, threads=128)
     p.tuning = dict(kernel=2, threads=128, stages=2, stage_kb=24, prefetch=1, producers=2)
     p.tuning = dict(kernel=3, threads=128, fund_per_thread=2)
     p.tuning = dict(kernel=2, threads=256, stages=2, stage_kb=96, producers=1)

@@ -59,7 +59,9 @@ def test_2d_full_size(hs, oracle_lib):
 # ---------------------------------------------------------------------------------------------
 # 1D adjoint
 # ---------------------------------------------------------------------------------------------
-def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True):
+def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True, sparse=0):
+    """Adjoint against the FP64 oracle; ``sparse`` > 0 keeps that many nonzero upstream
+    gradients per spectrum (as a top-k loss does) and zeroes the rest."""
     lengths = [len(x) for x in xs]
     flags = (hs.FLAG_WHITENING if w is not None else 0) | (0 if mitigation else hs.FLAG_NO_MITIGATION)
     plan = hs.Plan(H, form, lengths=lengths, dtype=dtype, flags=flags)
@@ -75,7 +77,15 @@ def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True):
     mu, sg = hs.norm_exponential(form, 1, H, mitigation)
     nrm = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
     out = plan.forward(xd, nrm if form == 1 else None, nrm if form == 2 else None, w=wd)[form]
-    g = torch.from_numpy(synth.upstream_grad(plan.total_fundamentals, 17)).to(DEV)
+    gh = synth.upstream_grad(plan.total_fundamentals, 17)
+    if sparse:
+        keep = np.zeros(gh.size, bool)
+        rng = np.random.default_rng(99)
+        for s in range(len(xs)):
+            a, b = int(plan.fund_offsets[s]), int(plan.fund_offsets[s + 1])
+            keep[rng.choice(np.arange(a, b), size=min(sparse, b - a), replace=False)] = True
+        gh = np.where(keep, gh, np.float32(0.0)).astype(np.float32)
+    g = torch.from_numpy(gh).to(DEV)
     gin = torch.zeros(plan.extent, dtype=torch.float32, device=DEV)
     gw = torch.zeros(len(xs[0]), dtype=torch.float32, device=DEV) if w is not None else None
     hs.backward(plan, form, g, out, xd, wd, gin, gw)
@@ -86,6 +96,12 @@ def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True):
     assert torch.equal(gin, gin2), "adjoint is not bit-reproducible"
     if gw is not None:
         assert torch.equal(gw, gw2)
+    else:
+        # without the workspace every block is visited: the same bits as with block marking
+        gin3 = torch.zeros_like(gin)
+        hs.backward(plan, form, g, out, xd, wd, gin3, None, mark_blocks=False)
+        torch.cuda.synchronize()
+        assert torch.equal(gin, gin3), "block marking changed the adjoint"
     gin = gin.cpu().numpy()
     gn = g.cpu().numpy().astype(np.float64)
     gw_ref = np.zeros(len(xs[0])) if w is not None else None
@@ -117,6 +133,23 @@ def bwd_case(hs, o, xs, H, form, w=None, dtype=0, mitigation=True):
 def test_backward_single(hs, oracle_lib, form, H):
     x = synth.spectrum(50001, 3 + H, [synth.Pulsar(401.2, 0.05)])
     bwd_case(hs, oracle_lib, [x], H, form)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_backward_sparse_gradient(hs, oracle_lib, form):
+    """A few nonzero upstream gradients per spectrum over uneven lengths: most bin blocks receive
+    nothing and are skipped."""
+    xs = [synth.spectrum(n, 40 + n % 97, [synth.Pulsar(77.7, 0.05)]) for n in (70001, 4099, 33, 1 << 17)]
+    bwd_case(hs, oracle_lib, xs, 32, form, sparse=16)
+    bwd_case(hs, oracle_lib, xs, 7, form, sparse=3)
+
+
+@pytest.mark.parametrize("dtype", [0, 2])
+def test_backward_sparse_whitening(hs, oracle_lib, dtype):
+    N = 1 << 15
+    w = synth.whitening(N, 4)
+    xs = [synth.spectrum(N, 80 + i, [synth.Pulsar(150.3 + i, 0.05)]) for i in range(5)]
+    bwd_case(hs, oracle_lib, xs, 32, 2, w=w, dtype=dtype, sparse=16)
 
 
 def test_backward_unmitigated_batch(hs, oracle_lib):
@@ -200,3 +233,68 @@ def test_autograd_topk_loss_matches_fd(hs, oracle_lib):
         assert abs(fd - gw[j]) <= 1e-4 * max(1.0, abs(fd)), (j, fd, gw[j])
         checked += 1
     assert checked >= 16
+
+
+def _f32_nearest(num: int, e2: int) -> np.float32:
+    """The float32 nearest to num * 2^e2 (ties to even), from exact rational arithmetic."""
+    from fractions import Fraction
+    exact = Fraction(num) * (Fraction(2) ** e2)
+    x0 = np.float32(float(exact))
+    best = None
+    for c in (np.nextafter(x0, np.float32(-np.inf)), x0, np.nextafter(x0, np.float32(np.inf))):
+        err = abs(Fraction(float(c)) - exact)
+        key = (err, int(np.array(c, np.float32).view(np.uint32)) & 1)
+        if best is None or key < best[0]:
+            best = (key, c)
+    return best[1]
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_backward_fixed_point_bit_exact(hs, oracle_lib, form):
+    """hs_backward's rounding rule, bit for bit: contributions c = fl32(g * fl32(1/sigma)) are
+    scaled to integers round(c * 2^(55 - e)), e the exponent of the largest |c| of the 1024-bin
+    block, summed exactly, and each bin's sum is rounded once to FP32."""
+    N, H, L = 30011, 32, 1024
+    x = synth.spectrum(N, 5 + form, [synth.Pulsar(123.4, 0.05)])
+    plan = hs.Plan(H, form, lengths=[N])
+    mu, sg = hs.norm_exponential(form, 1, H)
+    nrm = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    xd = torch.from_numpy(x).to(DEV)
+    out = plan.forward(xd, nrm if form == 1 else None, nrm if form == 2 else None)[form]
+    g = synth.upstream_grad(plan.total_fundamentals, 23)
+    gin = torch.zeros(plan.extent, dtype=torch.float32, device=DEV)
+    hs.backward(plan, form, torch.from_numpy(g).to(DEV), out, xd, None, gin, None)
+    torch.cuda.synchronize()
+    got = gin.cpu().numpy()[:N]
+    if form == 1:
+        _, bh = oracle_lib.simple_1d(x, H, mu, sg)
+        path = np.zeros(bh.size, np.uint64)
+    else:
+        _, bh, path = oracle_lib.greedy_1d(x, H, mu, sg)
+        path = path.astype(np.uint64)
+    assert np.array_equal(out.best_h.cpu().numpy(), bh)
+    rs = (np.float32(1.0) / sg.astype(np.float32)).astype(np.float32)
+    n = np.arange(bh.size, dtype=np.int64)
+    bins, vals = [], []
+    for k in range(1, H + 1):
+        sel = bh >= k
+        drift = np.zeros(bh.size, np.int64)
+        if form == 2:
+            mask = np.uint64((1 << k) - 1)
+            drift = np.array([bin(int(p & mask)).count("1") for p in path], np.int64)
+        bins.append((k * n + drift)[sel])
+        vals.append((g[sel].astype(np.float32) * rs[bh[sel] - 1]).astype(np.float32))
+    bins, vals = np.concatenate(bins), np.concatenate(vals)
+    blk = bins // L
+    vmax = np.zeros(N // L + 1)
+    np.maximum.at(vmax, blk, np.abs(vals.astype(np.float64)))
+    ex = np.frexp(vmax)[1] - 1                     # exponent e with 2^e <= vmax < 2^(e+1)
+    fixed = np.rint(vals.astype(np.float64) * np.ldexp(1.0, 55 - ex[blk])).astype(np.int64)
+    acc = np.zeros(N, np.int64)
+    np.add.at(acc, bins, fixed)
+    want = np.zeros(N, np.float32)
+    for j in np.nonzero(acc)[0]:
+        want[j] = _f32_nearest(int(acc[j]), int(ex[j // L]) - 55)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), \
+        f"{np.count_nonzero(got.view(np.uint32) != want.view(np.uint32))} bins differ"
+    plan.close()

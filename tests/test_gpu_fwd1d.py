@@ -95,7 +95,15 @@ TUNINGS = [dict(kernel=0, threads=256),
            dict(kernel=3, threads=128, fund_per_thread=2),
            dict(kernel=3, threads=64, fund_per_thread=2, ctas_per_sm=5),
            dict(kernel=4, threads=128),
-           dict(kernel=5, threads=256, ctas_per_sm=3, dynamic=1)]
+           dict(kernel=5, threads=256, ctas_per_sm=3, dynamic=1),
+           dict(kernel=6, threads=256),
+           dict(kernel=6, threads=128, ctas_per_sm=8, prefetch=1),
+           dict(kernel=7, threads=64, ctas_per_sm=6, dynamic=1, prefetch=1),
+           dict(kernel=7, threads=256, ctas_per_sm=2),
+           dict(kernel=7, threads=128, ctas_per_sm=16, prefetch=1),
+           dict(kernel=6, threads=192, ctas_per_sm=3, dynamic=1)]
+# one launch shape per kernel id, for the tests that sweep ids
+BY_KERNEL = {1: TUNINGS[1], 2: TUNINGS[5], 3: TUNINGS[10], 6: TUNINGS[14], 7: TUNINGS[16]}
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -105,13 +113,13 @@ def test_fused_f32_shapes(hs, oracle_lib, H, tuning):
     run_case(hs, oracle_lib, [x], H, tuning=tuning)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 6, 7])
 @pytest.mark.parametrize("forms", [1, 2, 3])
 @pytest.mark.parametrize("mitigation", [True, False])
 @pytest.mark.parametrize("dtype", [0, 1, 2])
 def test_forms_dtypes(hs, oracle_lib, forms, mitigation, dtype, kernel):
     x = synth.single_pulse_spectrum()
-    t = {1: TUNINGS[1], 2: TUNINGS[5], 3: TUNINGS[10]}[kernel]
+    t = BY_KERNEL[kernel]
     run_case(hs, oracle_lib, [x], 32, forms=forms, dtype=dtype, mitigation=mitigation, tuning=t)
 
 
@@ -121,19 +129,21 @@ def test_window_unaligned_tails(hs, oracle_lib, dtype, n):
     """Spectra whose last window ends off a 16-byte boundary at the very end of the input
     buffer: the bulk copy stops at the last whole 16-byte unit and the rest is loaded directly."""
     xs = [synth.spectrum(n - 7, 3), synth.spectrum(n, 4)]
-    for t in (TUNINGS[5], TUNINGS[6]):
+    for t in (TUNINGS[5], TUNINGS[6], TUNINGS[14], TUNINGS[16], TUNINGS[18]):
         run_case(hs, oracle_lib, xs, 7, dtype=dtype, tuning=t)
         run_case(hs, oracle_lib, xs, 32, dtype=dtype, tuning=t)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 3])
-def test_whitening(hs, oracle_lib, kernel):
-    N = 65536
+@pytest.mark.parametrize("kernel", [0, 1, 3, 6, 7])
+@pytest.mark.parametrize("N", [65536, 65533])
+def test_whitening(hs, oracle_lib, kernel, N):
+    """N = 65533: w and the spectra end off a 16-byte boundary."""
     w = synth.whitening(N, 5)
     xs = [synth.spectrum(N, 50 + i, [synth.Pulsar(300.4 + 17 * i, 0.07)]) for i in range(3)]
     for dtype in (0, 1, 2):
-        run_case(hs, oracle_lib, xs, 16, w=w, dtype=dtype,
-                 tuning=dict(kernel=kernel, threads=256, fund_per_thread=2 if kernel == 3 else 1))
+        for forms in (3, 2):
+            run_case(hs, oracle_lib, xs, 16, w=w, dtype=dtype, forms=forms,
+                     tuning=dict(kernel=kernel, threads=256, fund_per_thread=2 if kernel == 3 else 1))
 
 
 def test_small_and_degenerate_lengths(hs, oracle_lib):
@@ -148,7 +158,7 @@ def test_small_and_degenerate_lengths(hs, oracle_lib):
 def test_uneven_batch_per_spectrum_norm(hs, oracle_lib):
     b = synth.uneven_batch(count=24, seed=77, choices=(1 << 12, 1 << 13, 1 << 15, 1 << 17), pulsar_fraction=0.25)
     xs = [synth.batch_trial(b, i) for i in range(24)]
-    for t in (TUNINGS[1], TUNINGS[4], TUNINGS[5], TUNINGS[8]):
+    for t in (TUNINGS[1], TUNINGS[4], TUNINGS[5], TUNINGS[8], TUNINGS[15], TUNINGS[16]):
         run_case(hs, oracle_lib, xs, 16, per_spec_norm=True, tuning=t)
         run_case(hs, oracle_lib, xs, 16, dtype=1, tuning=t)
 
@@ -224,4 +234,12 @@ def test_long_spectrum_full_size(hs, oracle_lib):
     """The 2^23-bin, H = 32 single-spectrum workload in the default launch configuration."""
     x = synth.long_spectrum()
     near = run_case(hs, oracle_lib, [x], 32)
+    assert near <= 5
+
+
+@pytest.mark.parametrize("t", [TUNINGS[14], TUNINGS[15], TUNINGS[16], TUNINGS[19]])
+def test_long_spectrum_full_size_pair(hs, oracle_lib, t):
+    """The same workload through the paired-lane kernels (persistent, dynamic, L2 prefetch)."""
+    x = synth.long_spectrum()
+    near = run_case(hs, oracle_lib, [x], 32, tuning=t)
     assert near <= 5
