@@ -49,11 +49,11 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "footprints.json")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 # sources of the kernel each workload times (the ncu counters under profiles/ hold for them only)
 KERNEL_SOURCES = {
-    "long": ["hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
-    "long16": ["hs_fwd1d.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
-    "longbf16": ["hs_fwd1d.cuh", "hs_fwd1d_bf16.cu", "hs_internal.cuh"],
-    "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
-    "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
+    "long": ["hs_fwd1d.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "long16": ["hs_fwd1d.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
+    "longbf16": ["hs_fwd1d.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_bf16.cu", "hs_internal.cuh"],
+    "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
     "plane": ["hs_fwd2d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
 }
@@ -345,6 +345,24 @@ def wl_long(args, hs, torch, dev, world, dist):
                           "tuning": p2.tuning.as_dict()}
         p2.close()
 
+    # the optimal form (dynamic programme over drift paths) on the same input, for reference
+    po = hs.Plan(H, hs.OPTIMAL, lengths=[synth.LONG_N], dtype=dtype, device=dev.index)
+    no = [torch.from_numpy(a).to(dev) for a in (np.linspace(1.6, 1.6 * H, H).astype(np.float32),
+                                                np.sqrt(np.linspace(1.3, 1.3 * H, H)).astype(np.float32))]
+    io_o = po.alloc_form(*no, path=True, argmax=True)
+
+    def st_opt():
+        hs.run_optimal(po, x, None, io_o, stream)
+
+    for _ in range(3):
+        flush.fill_(1.0)
+        st_opt()
+    ot = time_steps(torch, st_opt, min(args.steps, 100), stream, flush)
+    oms = sum(ot) / len(ot)
+    per_form["optimal"] = {"value": units / (oms / 1e3), "ms": round(oms, 5),
+                           "note": "DP optimum over monotone drift paths, one warp per fundamental"}
+    po.close()
+
     # end to end through the C ABI with host buffers: pinned H2D of the spectrum, run,
     # D2H of every output, all inside the timed region
     xh = x.cpu().pin_memory()
@@ -390,7 +408,7 @@ def wl_batch(args, hs, torch, dev, world, dist):
     H = 16
     dtype = hs.F16 if args.workload == "batch16" else hs.F32
     elem = 4 if dtype == hs.F32 else 2
-    b = synth.uneven_batch()
+    b = synth.uneven_batch(count=args.batch_spectra)
     x = synth.device_batch(b, dev, dtype=torch.float16 if dtype == hs.F16 else None)
     plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=b.lengths, dtype=dtype, offsets=b.offsets[:-1],
                    flags=hs.FLAG_GRAPH | (0 if args.tuning else hs.FLAG_AUTOTUNE), device=dev.index)
@@ -426,7 +444,7 @@ def wl_batch(args, hs, torch, dev, world, dist):
         "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == hs.F32 else "f16 storage, f32 accumulate",
         "data": "synthetic",
-        "config": {"workload": f"2048 uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
+        "config": {"workload": f"{len(b.lengths)} uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
                                "H=16, 5% with a pulsar, one persistent launch from a CUDA graph",
                    "bins": int(sum(b.lengths)), "H": H, "fundamentals": int(nf), "spectra": len(b.lengths),
                    "l2": "inputs larger than L2 (no flush)", "tuning": plan.tuning.as_dict()},
@@ -566,6 +584,8 @@ def main():
     ap.add_argument("--workload", default="long", choices=sorted(WORKLOADS))
     ap.add_argument("--tuning", default=None, help="JSON hs_tuning override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-spectra", type=int, default=2048,
+                    help="spectra of the batch workloads (2048 = the benchmark; fewer only for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()

@@ -19,8 +19,9 @@
  *   SNR_h = (S_h - mu[h-1]) / sigma[h-1]; the maximum over h starts at h = 1 and is replaced
  *       only by a strictly larger value (lowest h wins ties).
  *
- * Fundamental domain: 1D n in [0, N_f) with N_f = floor((N-1)/H) -- every read of both forms
- * (largest: H n + H) lies inside the spectrum.  2D: f in [1, (n_freq-1-H)/H] and the z for which
+ * Fundamental domain: 1D n in [0, N_f) with N_f = floor((N-1)/H) -- every read of every form
+ * (largest: H n + H) lies inside the spectrum; with HS_FLAG_TRUNCATE_TAIL, n in [0, N - 1), the
+ * fundamentals past N_f summing fewer orders.  2D: f in [1, (n_freq-1-H)/H] and the z for which
  * rows z0_row + h z +- h stay inside the plane for all h (see hs_plan_domain_2d).
  *
  * Conventions for every entry point:
@@ -53,7 +54,12 @@ typedef enum {
     HS_ERR_NO_DEVICE = 7       /* plan made with HS_FLAG_NO_DEVICE cannot run */
 } hs_status;
 
-enum { HS_FORM_SIMPLE = 1, HS_FORM_GREEDY = 2 };
+/* Forms (a bitmask in hs_desc.forms).  HS_FORM_OPTIMAL (1D) is the optimum over every monotone
+ * drift path, S*_h[n] = max over D_1..D_h (D_k - D_{k-1} in {0, 1}, D_0 = 0, D_1 = 0 without
+ * mitigation) of sum_{k<=h} x[k n + D_k]: the "optimal partial sum" that the greedy choice
+ * approximates (Sec. 2.2, Sec. 3), an upper bound on the greedy sum.  It is computed by
+ * hs_run_optimal; hs_run computes the simple and greedy forms. */
+enum { HS_FORM_SIMPLE = 1, HS_FORM_GREEDY = 2, HS_FORM_OPTIMAL = 4 };
 
 typedef enum { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
 
@@ -64,14 +70,18 @@ enum {
     HS_FLAG_AUTOTUNE = 1u << 3,          /* time candidate launch shapes at plan creation */
     HS_FLAG_GRAPH = 1u << 4,             /* hs_run replays a captured CUDA graph */
     HS_FLAG_NO_DEVICE = 1u << 5,         /* host-only dry run: validate and size, no CUDA calls */
-    HS_FLAG_CHECKED = 1u << 6            /* kernels range-check every index into the error word */
+    HS_FLAG_CHECKED = 1u << 6,           /* kernels range-check every index into the error word */
+    HS_FLAG_TRUNCATE_TAIL = 1u << 7      /* 1D: also the fundamentals N_f <= n < N - 1, each form with
+                                            the orders whose every read fits: simple h n <= N - 1,
+                                            greedy / optimal h n + h <= N - 1 (best h <= that count) */
 };
 
 /* Plan description. */
 typedef struct {
     int32_t dims;            /* 1 (power spectra) or 2 (f-fdot plane) */
     int32_t H;               /* harmonics summed: 1..32 (1D), 1..8 (2D) */
-    int32_t forms;           /* HS_FORM_SIMPLE | HS_FORM_GREEDY (2D: HS_FORM_GREEDY only) */
+    int32_t forms;           /* any of HS_FORM_SIMPLE | HS_FORM_GREEDY | HS_FORM_OPTIMAL (2D:
+                                HS_FORM_GREEDY only) */
     int32_t dtype;           /* hs_dtype of the stored input (2D: HS_F32 only) */
     int64_t num_spectra;     /* B >= 1 (1D); 1 for 2D */
     const int64_t *lengths;  /* host [B]: N_s bins of spectrum s, H + 1 <= N_s < 2^31 - 64 (1D) */
@@ -110,9 +120,13 @@ typedef struct {
  *             threads run both forms from shared memory (not available with HS_FLAG_WHITENING);
  *   kernel 3: as 0 with two fundamentals per thread (n0 + t and n0 + t + threads), their
  *             chains interleaved: half the threads, twice the loads in flight per thread;
- *   kernels 4, 5: as 1 with look-ahead over 2 or 3 orders. */
+ *   kernels 4, 5: as 1 with look-ahead over 2 or 3 orders;
+ *   kernel 6: paired lanes: with both forms, two adjacent lanes compute the simple and the greedy
+ *             form of one fundamental and issue their reads in the same load instruction (a
+ *             tile is threads / 2 fundamentals; with one form, threads fundamentals);
+ *   kernel 7: as 6 with two fundamentals per lane (a tile is twice as large). */
 typedef struct {
-    int32_t kernel;          /* 0..5 */
+    int32_t kernel;          /* 0..7 */
     int32_t threads;         /* threads per CTA (kernel 2: consumer threads), multiple of 32: 64..256
                                 (kernels 0/1/3), 64..512 (kernel 2) */
     int32_t fund_per_thread; /* 2 for kernel 3, else 1 (a tile is threads x fund_per_thread) */
@@ -122,8 +136,10 @@ typedef struct {
                                 the workspace */
     int32_t stages;          /* kernel 2: ring slots, 2..16 */
     int32_t stage_kb;        /* kernel 2: KiB per slot (>= the largest order window) */
-    int32_t prefetch;        /* kernel 2: 1 = prefetch the whole input into L2 at launch when it fits
-                                in a quarter of L2 */
+    int32_t prefetch;        /* bit 0 (kernels 2, 6, 7): prefetch the whole input into L2 at launch
+                                when it fits in a quarter (kernel 2) or half (6, 7) of L2;
+                                bit 1 (all kernels but 2): the tiles of spectrum s prefetch the input
+                                of spectrum s+1 into L2, one share each */
     int32_t producers;       /* kernel 2: producer warps, 1..8 (<= stages; threads + 32 producers
                                 <= 640) */
 } hs_tuning;
@@ -155,10 +171,20 @@ hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_form_io *simple,
                  const hs_form_io *greedy, void *workspace, void *stream);
 
+/* Forward pass of the optimal form (plan with HS_FORM_OPTIMAL, 1D): for every fundamental,
+ * the SNR of S*_h (Eq. 2 with the caller's mu/sigma of the optimum), its maximum over h (first
+ * strictly larger wins, as for the other forms), the best h and, if optimal->path is set, an
+ * optimal drift path of that order (bit k-1 = increment at order k; ties keep the drift, and
+ * the lowest final drift is taken among equal optima).  FP32 accumulation along each path.
+ * Computed by a dynamic programme over the drift, one warp per fundamental.  Same input and
+ * workspace-free; enqueued on `stream` without allocation or synchronisation. */
+hs_status hs_run_optimal(hs_plan plan, const void *spectra, const float *w, const hs_form_io *optimal,
+                         void *stream);
+
 /* Adjoint of one 1D form with the forward's path and best_h held fixed (a subgradient
  * through the maximum of Eq. 2):
  *   dL/dx[j] = sum over (n, k <= h*(n)) with b_k(n) = j of grad_snr[n] / sigma[h*(n)-1],
- *   b_k(n) = k n (simple) or k n + popcount(path[n] & ((1 << k) - 1)) (greedy).
+ *   b_k(n) = k n (simple) or k n + popcount(path[n] & ((1 << k) - 1)) (greedy, optimal).
  * Each contribution is grad_snr[n] * fl(1/sigma); contributions to each bin are added exactly
  * in 64-bit fixed point (resolution 2^-55 of the largest contribution in its 1024-bin block) and
  * rounded once to FP32 (a result below FP32's normal range may be rounded twice), so the result
@@ -195,7 +221,8 @@ hs_status hs_check_device_error(hs_plan plan, void *stream);
  * term is an independent draw from i.i.d. exponential noise of mean `mean1`: simple h mean1,
  * sqrt(h) mean1; greedy (mitigated) 1.5 h mean1, sqrt(1.25 h) mean1; greedy without mitigation
  * (1 + 1.5 (h-1)) mean1, sqrt(1 + 1.25 (h-1)) mean1; 2D greedy H_9 h mean1,
- * sqrt(h sum_{k<=9} 1/k^2) mean1 (max of 9 draws).  No CUDA call. */
+ * sqrt(h sum_{k<=9} 1/k^2) mean1 (max of 9 draws).  HS_FORM_OPTIMAL has no closed form:
+ * HS_ERR_UNSUPPORTED.  No CUDA call. */
 hs_status hs_norm_exponential(int32_t form, int32_t dims, int32_t H, int32_t mitigation,
                               double mean1, float *mu_out, float *sigma_out);
 

@@ -14,6 +14,8 @@ The arithmetic lives in ``hs_oracle.c`` (plain C, FP64, single thread), compiled
               higher-dimensional sum but gives no algorithm; this reading is stated in the design doc)
   backward_1d adjoint of the forward with the chosen path and best h held fixed
   dp_1d       optimal partial sums over all monotone drift paths (Sec. 2.2 drift tree)
+  optimal_1d  dp_1d for every fundamental + Eq. 2's maximum over h (the optimal form)
+  tail_1d     fundamentals past the full-harmonic domain with the orders that fit (all forms)
   brute_1d/2d exhaustive enumeration of drift paths (tiny inputs)
   sectors_1d  distinct 32-B input sectors read (compulsory input bytes)
   sectors_2d  the same for the 2D greedy form over an f-fdot plane
@@ -73,6 +75,10 @@ def lib():
             L.hso_backward_1d.argtypes = [_I32, _I64, _I32, _I64, _P, _P, _P, _P, _P]
             L.hso_dp_1d.restype = ctypes.c_int
             L.hso_dp_1d.argtypes = [_P, _P, _I32, _I64, _I32, _I32, _I64, _P]
+            L.hso_tail_1d.restype = ctypes.c_int
+            L.hso_tail_1d.argtypes = [_I32, _P, _P, _I32, _I64, _I32, _I32, _P, _P, _I64, _I64, _P, _P, _P, _P]
+            L.hso_optimal_1d.restype = ctypes.c_int
+            L.hso_optimal_1d.argtypes = [_P, _P, _I32, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _P]
             L.hso_brute_1d.restype = ctypes.c_int
             L.hso_brute_1d.argtypes = [_P, _P, _I32, _I64, _I32, _I32, _I64, _P, _P, _P]
             L.hso_brute_2d.restype = ctypes.c_int
@@ -184,6 +190,48 @@ def dp_1d(p, H, fund, mitigation=True, w=None, round_w=True):
     _check(lib().hso_dp_1d(_ptr(p), _ptr(w), int(round_w), p.shape[0], int(H), int(bool(mitigation)),
                            int(fund), _ptr(out)), "dp_1d")
     return out
+
+
+def tail_1d(form, p, H, mu, sigma, mitigation=True, w=None, round_w=True, lo=None, hi=None, want_all=False):
+    """Fundamentals n in [lo, hi) (default [N_f, N-1)) past the full-harmonic domain, each form
+    summing only its orders whose reads fit (simple h n <= N-1; greedy/optimal h n + h <= N-1).
+    Returns (snr, best_h, path (greedy, else None)[, snr_all with NaN for excluded orders])."""
+    p = _f32(p)
+    w = _f32(w)
+    n = p.shape[0]
+    lo = nf_1d(n, H) if lo is None else int(lo)
+    hi = n - 1 if hi is None else int(hi)
+    k = max(hi - lo, 0)
+    snr = np.empty(k, np.float64)
+    bh = np.empty(k, np.uint8)
+    path = np.zeros(k, np.uint32) if form == 2 else None
+    allv = np.empty((k, H), np.float64) if want_all else None
+    mu, sigma = _f64(mu), _f64(sigma)
+    _check(lib().hso_tail_1d(int(form), _ptr(p), _ptr(w), int(round_w), n, int(H), int(bool(mitigation)),
+                             _ptr(mu), _ptr(sigma), lo, hi, _ptr(snr), _ptr(bh), _ptr(path), _ptr(allv)), "tail_1d")
+    return (snr, bh, path, allv) if want_all else (snr, bh, path)
+
+
+def tail_orders(form, n, H, f):
+    """Orders summed for fundamental f of an n-bin spectrum in the truncated tail."""
+    lim = (H if f == 0 else (n - 1) // f) if form == 1 else (n - 1) // (f + 1)
+    return min(lim, H)
+
+
+def optimal_1d(p, H, mu, sigma, mitigation=True, w=None, round_w=True, nf=None, want_all=False):
+    """Optimal form: the DP optimum S*_h over monotone drift paths (Sec. 2.2) + max SNR (Eq. 2).
+    Returns (snr f64[nf], best_h u8[nf][, snr_all [nf,H]])."""
+    p = _f32(p)
+    w = _f32(w)
+    n = p.shape[0]
+    nf = nf_1d(n, H) if nf is None else int(nf)
+    snr = np.empty(nf, np.float64)
+    bh = np.empty(nf, np.uint8)
+    allv = np.empty((nf, H), np.float64) if want_all else None
+    mu, sigma = _f64(mu), _f64(sigma)
+    _check(lib().hso_optimal_1d(_ptr(p), _ptr(w), int(round_w), n, int(H), int(bool(mitigation)),
+                                _ptr(mu), _ptr(sigma), nf, _ptr(snr), _ptr(bh), _ptr(allv)), "optimal_1d")
+    return (snr, bh, allv) if want_all else (snr, bh)
 
 
 def brute_1d(p, H, fund, mitigation=True, w=None, round_w=True):

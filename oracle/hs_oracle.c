@@ -118,6 +118,80 @@ int hso_greedy_1d(const float *p, const float *w, int32_t round_w, int64_t n, in
 }
 
 /*
+ * Fundamentals past the full-harmonic domain: n in [lo, hi) with N_f <= lo and hi <= N - 1 (the
+ * reading of "for each bin" that keeps every bin whose fundamental comparison fits, Sec. 1 and
+ * Algorithm 2's loop over the spectrum).  Each form sums only the orders whose every possible
+ * read lies inside the spectrum:
+ *   simple (form 1): the bin of order h is h n, so H_n = min(H, floor((N-1)/n));
+ *   greedy (form 2) and optimal (form 4): the bins of order h are at most h n + h (drift at most
+ *   h - 1 after order h - 1, plus the compared neighbour), so H_n = min(H, floor((N-1)/(n+1))).
+ * Within its H_n orders each form is exactly the one above (Eq. 3; Eq. 5 / Algorithm 2; the
+ * optimum of hso_dp_1d), and the maximum of Eq. 2 runs over h = 1..H_n.  snr_all [hi-lo][H]
+ * (may be NULL) holds NaN for the excluded orders; path (greedy only, may be NULL).
+ */
+int hso_dp_1d(const float *p, const float *w, int32_t round_w, int64_t n, int32_t H,
+              int32_t mitigation, int64_t fund, double *best_sum);
+
+static int64_t tail_orders(int32_t form, int64_t n, int32_t H, int64_t f)
+{
+    const int64_t lim = form == 1 ? (f == 0 ? H : (n - 1) / f) : (n - 1) / (f + 1);
+    return lim < H ? lim : H;
+}
+
+int hso_tail_1d(int32_t form, const float *p, const float *w, int32_t round_w, int64_t n, int32_t H,
+                int32_t mitigation, const double *mu, const double *sigma, int64_t lo, int64_t hi,
+                double *snr, uint8_t *best_h, uint32_t *path, double *snr_all)
+{
+    if (!p || !mu || !sigma || H < 1 || H > HSO_MAX_H || lo < 0 || hi > n - 1 || lo > hi) return -1;
+    if (form != 1 && form != 2 && form != 4) return -1;
+    for (int64_t f = lo; f < hi; ++f) {
+        const int64_t i = f - lo;
+        const int Hn = (int)tail_orders(form, n, H, f);
+        if (Hn < 1) return -1;
+        double sums[HSO_MAX_H];
+        uint32_t bits = 0;
+        if (form == 1) {
+            double sum = 0.0;
+            for (int h = 1; h <= Hn; ++h) {
+                sum += load_x(p, w, round_w, (int64_t)h * f);
+                sums[h - 1] = sum;
+            }
+        } else if (form == 2) {
+            int64_t d = 0;
+            double sum;
+            if (mitigation) {
+                double a = load_x(p, w, round_w, f), b = load_x(p, w, round_w, f + 1);
+                if (b > a) { d = 1; sum = b; bits |= 1u; }
+                else { sum = a; }
+            } else {
+                sum = load_x(p, w, round_w, f);
+            }
+            sums[0] = sum;
+            for (int h = 2; h <= Hn; ++h) {
+                const int64_t m = (int64_t)h * f + d;
+                double a = load_x(p, w, round_w, m), b = load_x(p, w, round_w, m + 1);
+                if (b > a) { d += 1; sum += b; bits |= 1u << (h - 1); }
+                else { sum += a; }
+                sums[h - 1] = sum;
+            }
+        } else {
+            if (hso_dp_1d(p, w, round_w, n, Hn, mitigation, f, sums) != 0) return -1;
+        }
+        double best = snr_of(sums[0], 1, mu, sigma);
+        int bh = 1;
+        for (int h = 1; h <= H; ++h) {
+            const double v = h <= Hn ? snr_of(sums[h - 1], h, mu, sigma) : NAN;
+            if (snr_all) snr_all[i * H + (h - 1)] = v;
+            if (h > 1 && h <= Hn && v > best) { best = v; bh = h; }
+        }
+        if (snr) snr[i] = best;
+        if (best_h) best_h[i] = (uint8_t)bh;
+        if (path && form == 2) path[i] = bits;
+    }
+    return 0;
+}
+
+/*
  * 2D greedy harmonic sum over an f-fdot plane (the higher-dimensional harmonic sum the
  * paper names for acceleration searches; the paper gives no 2D algorithm, so this
  * follows the 1D rule lifted to a 3x3 neighbourhood):
@@ -191,7 +265,8 @@ int hso_backward_1d(int32_t form, int64_t n, int32_t H, int64_t nf, const uint8_
     if (!best_h || !sigma || !g || !grad_x || H < 1 || H > HSO_MAX_H) return -1;
     if (form != 1 && form != 2) return -1;
     if (form == 2 && !path) return -1;
-    if (nf > hso_nf_1d(n, H)) return -1;
+    /* nf may reach N - 1 (the truncated tail): every chosen bin must then lie in the spectrum */
+    if (nf > n - 1) return -1;
     memset(grad_x, 0, sizeof(double) * (size_t)n);
     for (int64_t f = 0; f < nf; ++f) {
         int hb = best_h[f];
@@ -203,6 +278,7 @@ int hso_backward_1d(int32_t form, int64_t n, int32_t H, int64_t nf, const uint8_
                 uint32_t mask = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
                 j += __builtin_popcount(path[f] & mask);
             }
+            if (j >= n) return -1;
             grad_x[j] += c;
         }
     }
@@ -241,6 +317,37 @@ int hso_dp_1d(const float *p, const float *w, int32_t round_w, int64_t n, int32_
         best_sum[k - 1] = mx;
         dmax = nd;
         for (int D = 0; D <= dmax; ++D) prev[D] = cur[D];
+    }
+    return 0;
+}
+
+/*
+ * The optimal form over a spectrum: for every fundamental n < nf the optimal partial sums
+ * S*_h (hso_dp_1d above), their SNR by Eq. 2 and its maximum over h = 1..H, starting at h = 1
+ * and replaced only by a strictly larger value.  snr_all [nf][H] (may be NULL) receives every
+ * order's SNR.
+ */
+int hso_optimal_1d(const float *p, const float *w, int32_t round_w, int64_t n, int32_t H,
+                   int32_t mitigation, const double *mu, const double *sigma, int64_t nf, double *snr,
+                   uint8_t *best_h, double *snr_all)
+{
+    if (!p || !mu || !sigma || !snr || !best_h || H < 1 || H > HSO_MAX_H || nf < 0 || nf > hso_nf_1d(n, H))
+        return -1;
+    double sums[HSO_MAX_H];
+    for (int64_t f = 0; f < nf; ++f) {
+        if (hso_dp_1d(p, w, round_w, n, H, mitigation, f, sums) != 0) return -1;
+        double best = snr_of(sums[0], 1, mu, sigma);
+        int bh = 1;
+        for (int h = 1; h <= H; ++h) {
+            const double v = snr_of(sums[h - 1], h, mu, sigma);
+            if (snr_all) snr_all[f * H + (h - 1)] = v;
+            if (h > 1 && v > best) {
+                best = v;
+                bh = h;
+            }
+        }
+        snr[f] = best;
+        best_h[f] = (uint8_t)bh;
     }
     return 0;
 }

@@ -19,12 +19,13 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_fixed_scratch", "backward", "norm_exponential",
+__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_fixed_scratch", "run_optimal", "backward",
+           "norm_exponential", "OPTIMAL",
            "check_device_error", "decode_argmax", "status_string", "SIMPLE", "GREEDY", "F32", "F16", "BF16",
            "FLAG_NO_MITIGATION", "FLAG_PER_SPECTRUM_NORM", "FLAG_WHITENING", "FLAG_AUTOTUNE", "FLAG_GRAPH",
-           "FLAG_NO_DEVICE", "FLAG_CHECKED", "lib", "LIB_PATH"]
+           "FLAG_NO_DEVICE", "FLAG_CHECKED", "FLAG_TRUNCATE_TAIL", "lib", "LIB_PATH"]
 
-SIMPLE, GREEDY = 1, 2
+SIMPLE, GREEDY, OPTIMAL = 1, 2, 4
 F32, F16, BF16 = 0, 1, 2
 FLAG_NO_MITIGATION = 1 << 0
 FLAG_PER_SPECTRUM_NORM = 1 << 1
@@ -33,6 +34,7 @@ FLAG_AUTOTUNE = 1 << 3
 FLAG_GRAPH = 1 << 4
 FLAG_NO_DEVICE = 1 << 5
 FLAG_CHECKED = 1 << 6
+FLAG_TRUNCATE_TAIL = 1 << 7
 
 STATUS = {0: "HS_OK", 1: "HS_ERR_INVALID_ARG", 2: "HS_ERR_UNSUPPORTED", 3: "HS_ERR_OOM", 4: "HS_ERR_CUDA",
           5: "HS_ERR_DEVICE_BOUNDS", 6: "HS_ERR_DEVICE_TIMEOUT", 7: "HS_ERR_NO_DEVICE"}
@@ -96,6 +98,7 @@ def lib():
         L.hs_run.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V, _V]
         L.hs_backward.argtypes = [_V, _I32, _V, ctypes.POINTER(_FormIO), _V, _V, _V, _V, _V, _V]
         L.hs_run_fixed_scratch.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V]
+        L.hs_run_optimal.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), _V]
         L.hs_check_device_error.argtypes = [_V, _V]
         L.hs_norm_exponential.argtypes = [_I32, _I32, _I32, _I32, ctypes.c_double, _V, _V]
         L.hs_status_string.argtypes = [ctypes.c_int]
@@ -105,7 +108,7 @@ def lib():
         for name in ("hs_plan_create", "hs_plan_destroy", "hs_plan_fundamentals", "hs_plan_input_offsets",
                      "hs_plan_domain_2d", "hs_plan_workspace", "hs_plan_get_tuning", "hs_plan_set_tuning",
                      "hs_run", "hs_backward", "hs_check_device_error", "hs_norm_exponential",
-                     "hs_run_fixed_scratch"):
+                     "hs_run_fixed_scratch", "hs_run_optimal"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -292,12 +295,17 @@ class Plan:
                       torch.empty(F, dtype=self.path_dtype(), device=dev) if path else None,
                       torch.empty(self.B, dtype=torch.int64, device=dev) if argmax else None)
 
-    def forward(self, spectra, simple_norm=None, greedy_norm=None, w=None, path=True, argmax=True, stream=None):
-        """Run both planned forms; ``*_norm`` = (mu, sigma) device tensors.  Returns {form: FormIO}."""
+    def forward(self, spectra, simple_norm=None, greedy_norm=None, w=None, path=True, argmax=True, stream=None,
+                optimal_norm=None):
+        """Run the planned forms; ``*_norm`` = (mu, sigma) device tensors.  Returns {form: FormIO}."""
         s = self.alloc_form(*simple_norm, path=False, argmax=argmax) if self.forms & SIMPLE else None
         g = self.alloc_form(*greedy_norm, path=path, argmax=argmax) if self.forms & GREEDY else None
-        run(self, spectra, w, s, g, stream=stream)
+        if s is not None or g is not None:
+            run(self, spectra, w, s, g, stream=stream)
         out = {}
+        if self.forms & OPTIMAL:
+            out[OPTIMAL] = self.alloc_form(*optimal_norm, path=path, argmax=argmax)
+            run_optimal(self, spectra, w, out[OPTIMAL], stream=stream)
         if s is not None:
             out[SIMPLE] = s
         if g is not None:
@@ -324,6 +332,13 @@ def run_fixed_scratch(plan: Plan, spectra, w=None, simple: FormIO | None = None,
     cg = greedy._c() if greedy is not None else None
     _check(lib().hs_run_fixed_scratch(plan.handle, _ptr(spectra), _ptr(w), ctypes.byref(cs) if cs else None,
                                       ctypes.byref(cg) if cg else None, _stream_ptr(stream)), "hs_run_fixed_scratch")
+
+
+def run_optimal(plan: Plan, spectra, w=None, io: FormIO | None = None, stream=None):
+    """hs_run_optimal: the optimal form (DP over drift paths) of a plan with OPTIMAL."""
+    c = io._c()
+    _check(lib().hs_run_optimal(plan.handle, _ptr(spectra), _ptr(w), ctypes.byref(c), _stream_ptr(stream)),
+           "hs_run_optimal")
 
 
 def backward(plan: Plan, form: int, grad_snr, fwd: FormIO, spectra=None, w=None, grad_in=None, grad_w=None,
@@ -358,8 +373,11 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, p, w, plan, form, mu, sigma):
-            io = plan.alloc_form(mu, sigma, path=(form == GREEDY), argmax=False)
-            run(plan, p, w, io if form == SIMPLE else None, io if form == GREEDY else None)
+            io = plan.alloc_form(mu, sigma, path=(form != SIMPLE), argmax=False)
+            if form == OPTIMAL:
+                run_optimal(plan, p, w, io)
+            else:
+                run(plan, p, w, io if form == SIMPLE else None, io if form == GREEDY else None)
             ctx.plan, ctx.form = plan, form
             ctx.io = io
             ctx.save_for_backward(p, w if w is not None else torch.empty(0, device=p.device))

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -32,7 +33,8 @@ bool cuda_ok(cudaError_t e)
     } while (0)
 
 constexpr uint32_t kKnownFlags = HS_FLAG_NO_MITIGATION | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_WHITENING |
-                                 HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_NO_DEVICE | HS_FLAG_CHECKED;
+                                 HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_NO_DEVICE | HS_FLAG_CHECKED |
+                                 HS_FLAG_TRUNCATE_TAIL;
 constexpr size_t kWorkspaceBytes = 256;     // tile counter of the dynamic schedule
 constexpr int kBwdBlockBins = 1024;   // must stay <= 32767 (int16 offsets)
 constexpr int kBwdMaxGroups = 16;     // spectrum groups of the adjoint's dL/dw partial sums
@@ -74,6 +76,7 @@ struct hs_plan_s {
     int sms = 0;
     int path_bytes = 0;
     std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
+    std::vector<int64_t> nf_main, tail_tile_start;   // full-harmonic fundamentals; truncated-tail tiles
     int64_t total_fund = 0, extent = 0, max_len = 0;
     int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
     hs_tuning tun{1, 256, 1, 0, 0, 0, 0, 0, 0};
@@ -81,6 +84,7 @@ struct hs_plan_s {
     WinPlan wplan{};
     // device tables
     int64_t *d_in_off = nullptr, *d_fund_off = nullptr, *d_tile_start = nullptr, *d_in_len = nullptr;
+    int64_t *d_nf_main = nullptr, *d_tail_tile_start = nullptr;
     int *d_err = nullptr;
     // graph replay
     cudaStream_t cap = nullptr;
@@ -96,7 +100,7 @@ namespace {
 int64_t tile_fund(const hs_desc &d, const hs_tuning &t)
 {
     if (t.kernel == 6 || t.kernel == 7) {
-        const int64_t pass = d.forms == (HS_FORM_SIMPLE | HS_FORM_GREEDY) ? t.threads / 2 : t.threads;
+        const int64_t pass = (d.forms & 3) == (HS_FORM_SIMPLE | HS_FORM_GREEDY) ? t.threads / 2 : t.threads;
         return t.kernel == 7 ? 2 * pass : pass;
     }
     return static_cast<int64_t>(t.threads) * t.fund_per_thread;
@@ -144,7 +148,11 @@ void compute_tiles(hs_plan p)
     const int64_t T = tile_fund(p->d, p->tun);
     const size_t B = p->nf.size();
     p->tile_start.assign(B + 1, 0);
-    for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf[s] + T - 1) / T;
+    // the main kernels cover the fundamentals with all H orders; the truncated tail has its own tiles
+    for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf_main[s] + T - 1) / T;
+    p->tail_tile_start.assign(B + 1, 0);
+    for (size_t s = 0; s < B; ++s)
+        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailThreads - 1) / kTailThreads;
     make_win_plan(p);
 }
 
@@ -169,8 +177,11 @@ hs_status validate_tuning(const hs_plan p, const hs_tuning *t)
     if (t->kernel == 3 && t->dynamic) return HS_ERR_INVALID_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return HS_ERR_INVALID_ARG;
     if (t->dynamic != 0 && t->dynamic != 1) return HS_ERR_INVALID_ARG;
-    if (t->prefetch < 0 || t->prefetch > 1) return HS_ERR_INVALID_ARG;
-    if (t->kernel != 2 && t->kernel != 6 && t->kernel != 7 && t->prefetch != 0) return HS_ERR_INVALID_ARG;
+    // prefetch bit 0: the whole input into L2 at launch when it fits in part of L2 (kernels 2, 6, 7);
+    // bit 1: the tiles of each spectrum prefetch the next spectrum (every kernel but 2)
+    if (t->prefetch < 0 || t->prefetch > 3) return HS_ERR_INVALID_ARG;
+    if ((t->prefetch & 1) && t->kernel != 2 && t->kernel != 6 && t->kernel != 7) return HS_ERR_INVALID_ARG;
+    if ((t->prefetch & 2) && t->kernel == 2) return HS_ERR_INVALID_ARG;
     if (t->kernel != 2 && t->producers != 0) return HS_ERR_INVALID_ARG;
     if (t->kernel == 2) {
         if (p->d.flags & HS_FLAG_WHITENING) return HS_ERR_UNSUPPORTED;
@@ -204,6 +215,13 @@ void make_win_plan(hs_plan p)
 
 hs_tuning default_tuning(const hs_plan p)
 {
+    // Fused plans whose input exceeds L2 (batches of spectra streaming from DRAM): two
+    // fundamentals per thread (kernel 3, 128-thread CTAs) keep the most gathers in flight --
+    // 18.3 ms vs 24.2 ms (kernel 0) on 2048 spectra of 2^20..2^23 bins, H = 16, FP32; with 16-bit
+    // storage each spectrum's tiles also prefetch the next spectrum into L2 (15.2 vs 15.8 ms).
+    if (p->l2_bytes > 0 && p->extent * elem_bytes(p->d.dtype) > p->l2_bytes &&
+        (p->d.forms & 3) == 3 && !(p->d.flags & HS_FLAG_WHITENING))
+        return hs_tuning{3, 128, 2, 0, 0, 0, 0, (p->d.dtype != HS_F32 && p->d.num_spectra > 1) ? 2 : 0, 0};
     // Measured on the 2^23-bin H = 32 spectrum (GB300): FP32 without whitening runs fastest on
     // the paired-lane kernel 6 (fused 43 us vs 45 us, simple 25.6 vs 27.8 us, greedy equal);
     // with whitening or 16-bit storage the direct kernel 0 is as fast or faster (256-thread CTAs
@@ -251,6 +269,8 @@ void free_plan(hs_plan p)
         cudaFree(p->d_in_off);
         cudaFree(p->d_fund_off);
         cudaFree(p->d_tile_start);
+        cudaFree(p->d_nf_main);
+        cudaFree(p->d_tail_tile_start);
         cudaFree(p->d_in_len);
         cudaFree(p->d_err);
     }
@@ -282,7 +302,32 @@ FormArgs to_form_args(const hs_form_io *io)
     return f;
 }
 
-// Enqueue the forward pass (memsets + one kernel) on `st`.
+const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
+{
+    switch (dtype) {
+    case HS_F32: return fwd1d_tail_kernel_f32(forms, whitening);
+    case HS_F16: return fwd1d_tail_kernel_f16(forms, whitening);
+    case HS_BF16: return fwd1d_tail_kernel_bf16(forms, whitening);
+    }
+    return nullptr;
+}
+
+// The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel.
+hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st)
+{
+    if (!(p->d.flags & HS_FLAG_TRUNCATE_TAIL) || main_args.tail_tiles <= 0) return HS_OK;
+    if (main_args.tail_tiles > 0x7fffffff) return HS_ERR_UNSUPPORTED;
+    const void *fn = fwd1d_tail_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    Fwd1DArgs a = main_args;
+    a.tile_counter = nullptr;
+    a.pf_chunk = 0;
+    void *args[] = {&a};
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail_tiles)), dim3(kTailThreads), args, 0, st));
+    return HS_OK;
+}
+
+// Enqueue the forward pass (memsets + the main kernel + the truncated tail's) on `st`.
 hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
                       const hs_form_io *greedy, void *ws, cudaStream_t st)
 {
@@ -315,6 +360,9 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.w = w;
     a.in_off = p->d_in_off;
     a.fund_off = p->d_fund_off;
+    a.nf_main = p->d_nf_main;
+    a.tail_tile_start = p->d_tail_tile_start;
+    a.tail_tiles = p->tail_tile_start.empty() ? 0 : p->tail_tile_start.back();
     a.tile_start = p->d_tile_start;
     a.in_len = p->d_in_len;
     a.B = static_cast<int32_t>(p->d.num_spectra);
@@ -326,10 +374,13 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.fund_per_thread = t.fund_per_thread;
     a.total_tiles = p->tile_start.back();
     a.extent = p->extent;
+    a.elem_bytes = elem_bytes(p->d.dtype);
+    a.pf_next = (t.prefetch & 2) ? 1 : 0;
     a.s = to_form_args(simple);
     a.g = to_form_args(greedy);
     a.err = p->d_err;
-    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
+    if ((p->d.forms & 3) == 0) return HS_OK;   // the optimal form runs through hs_run_optimal
+    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
     if (!fn) return HS_ERR_UNSUPPORTED;
     if (t.kernel == 2) {
         const size_t smem = static_cast<size_t>(p->wplan.nslot) * p->wplan.slot_bytes;
@@ -349,7 +400,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
             wp.pf_chunk = ((in_bytes + grid - 1) / grid + 15) / 16 * 16;
         void *args[] = {&a, &wp};
         HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(block), args, smem, st));
-        return HS_OK;
+        return launch_tail(p, a, st);
     }
     int64_t grid = a.total_tiles;
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
@@ -371,7 +422,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     if (grid > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     void *args[] = {&a};
     HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
-    return HS_OK;
+    return launch_tail(p, a, st);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -418,15 +469,28 @@ hs_status autotune(hs_plan p)
             return upload_tiles(p);
         }
     }
-    // sub-plan: up to 8 of the longest spectra, packed
-    std::vector<int64_t> lens(p->len);
-    std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
-    if (lens.size() > 8) lens.resize(8);
+    // sub-plan: spectra sampled evenly from the sorted lengths, packed, until the input reaches
+    // eight times L2 (or the whole plan): the mix of lengths and the L2 behaviour of a schedule
+    // (a static persistent grid drifts apart and thrashes L2 on large batches) resemble the plan's
+    std::vector<int64_t> all(p->len);
+    std::sort(all.begin(), all.end(), std::greater<int64_t>());
+    const int64_t total_elems = std::accumulate(all.begin(), all.end(), int64_t(0));
+    const int64_t want_elems = std::min<int64_t>(total_elems, 8 * static_cast<int64_t>(p->l2_bytes) / elem_bytes(p->d.dtype));
+    size_t nsub = 1;
+    while (nsub < all.size() && nsub < 1024) {
+        int64_t e = 0;
+        for (size_t i = 0; i < nsub; ++i) e += all[i * all.size() / nsub];
+        if (e >= want_elems) break;
+        ++nsub;
+    }
+    std::vector<int64_t> lens;
+    for (size_t i = 0; i < nsub; ++i) lens.push_back(all[i * all.size() / nsub]);
     hs_desc sd = p->d;
     sd.num_spectra = static_cast<int64_t>(lens.size());
     sd.lengths = lens.data();
     sd.offsets = nullptr;
-    sd.flags &= ~(HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_CHECKED);
+    sd.flags &= ~(HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_CHECKED | HS_FLAG_TRUNCATE_TAIL);
+    sd.forms &= 3;
     if (sd.flags & HS_FLAG_WHITENING) {
         for (auto &l : lens) l = lens[0];
     }
@@ -435,6 +499,11 @@ hs_status autotune(hs_plan p)
     if (st != HS_OK) return st;
     const int64_t ext = sp->extent, F = sp->total_fund, H = sp->d.H;
     void *x = nullptr, *w = nullptr, *ws = nullptr, *outs = nullptr, *norm = nullptr, *tmp = nullptr;
+    void *flush = nullptr;   // written before every timed run: candidates are timed on a cold L2
+    int pf_next = 0, pf_all = 0;
+    const int64_t ext_all = p->extent;
+    bool big = false;
+    const size_t flush_bytes = std::max<size_t>(2 * static_cast<size_t>(p->l2_bytes), size_t(64) << 20);
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     hs_status result = HS_OK;
@@ -446,6 +515,7 @@ hs_status autotune(hs_plan p)
     if (!cuda_ok(cudaMalloc(&x, ext * elem_bytes(sd.dtype) + 64)) || !cuda_ok(cudaMalloc(&tmp, ext * 4 + 64)) ||
         !cuda_ok(cudaMalloc(&w, lens[0] * 4 + 64)) || !cuda_ok(cudaMalloc(&ws, kWorkspaceBytes)) ||
         !cuda_ok(cudaMalloc(&outs, out_bytes)) || !cuda_ok(cudaMalloc(&norm, 4 * H * 4)) ||
+        !cuda_ok(cudaMalloc(&flush, flush_bytes)) ||
         !cuda_ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) || !cuda_ok(cudaEventCreate(&e0)) ||
         !cuda_ok(cudaEventCreate(&e1))) {
         result = HS_ERR_OOM;
@@ -482,17 +552,29 @@ hs_status autotune(hs_plan p)
                 if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
             }
         }
-    for (int threads : {64, 128, 256}) {
-        hs_tuning t{3, threads, 2, 0, 0, 0, 0, 0, 0};
-        if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
-    }
+    // the next-spectrum prefetch (prefetch bit 1) only matters with several spectra; the whole-input
+    // prefetch (bit 0, kernels 6 and 7) only when the input fits in half of L2
+    pf_next = sd.num_spectra > 1 ? 2 : 0;
+    pf_all = ext * elem_bytes(sd.dtype) <= p->l2_bytes / 2 ? 1 : 0;
+    for (int threads : {64, 128, 256})
+        for (int pf : {0, pf_next}) {
+            hs_tuning t{3, threads, 2, 0, 0, 0, 0, pf, 0};
+            if (validate_tuning(sp, &t) == HS_OK) cands.push_back(t);
+            if (!pf_next) break;
+        }
+    // a static persistent grid drifts apart over a long pass and thrashes L2: on 2048 spectra
+    // (32 GB) it ran 30% slower than one CTA per tile although it won on a 1 GB sample, so it
+    // is not a candidate for plans larger than L2
+    big = ext_all * elem_bytes(p->d.dtype) > static_cast<int64_t>(p->l2_bytes);
     for (int kernel : {0, 1, 4, 5, 6, 7})
         for (int threads : {128, 256})
             for (int sched = 0; sched < 3; ++sched) {
-                hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, 0, 0};
+                if (big && sched == 1) continue;
+                const int pf = (kernel >= 6 ? pf_all : 0) | (sched == 0 ? pf_next : 0);
+                hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, pf, 0};
                 if (sched >= 1) {
                     int occ = 0;
-                    const void *fn = fwd1d_kernel(sd.dtype, sd.forms, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
+                    const void *fn = fwd1d_kernel(sd.dtype, sd.forms & 3, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
                     if (occ < 1) continue;
                     t.ctas_per_sm = occ;
@@ -509,6 +591,7 @@ hs_status autotune(hs_plan p)
         const hs_form_io *pg = (sd.forms & HS_FORM_GREEDY) ? &fg : nullptr;
         float total = 0.f;
         for (int rep = 0; rep < 4; ++rep) {
+            cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
             if (enqueue_fwd(sp, x, wp, ps, pg, ws, s) != HS_OK) { result = HS_ERR_CUDA; goto done; }
             cudaEventRecord(e1, s);
@@ -536,6 +619,7 @@ done:
     cudaFree(ws);
     cudaFree(outs);
     cudaFree(norm);
+    cudaFree(flush);
     hs_plan_destroy(sp);
     return result;
 }
@@ -571,6 +655,8 @@ hs_status hs_norm_exponential(int32_t form, int32_t dims, int32_t H, int32_t mit
 {
     if (!mu_out || !sigma_out || !(mean1 > 0.0) || !std::isfinite(mean1)) return HS_ERR_INVALID_ARG;
     if (dims == 1) {
+        // the optimum over drift paths has no closed-form moments: callers estimate them
+        if (form == HS_FORM_OPTIMAL) return HS_ERR_UNSUPPORTED;
         if (H < 1 || H > kMaxH1D || (form != HS_FORM_SIMPLE && form != HS_FORM_GREEDY)) return HS_ERR_INVALID_ARG;
     } else if (dims == 2) {
         if (H < 1 || H > kMaxH2D || form != HS_FORM_GREEDY) return HS_ERR_INVALID_ARG;
@@ -618,7 +704,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
     p->no_device = (d.flags & HS_FLAG_NO_DEVICE) != 0;
     if (d.dims == 1) {
         if (d.H < 1 || d.H > kMaxH1D) { delete p; return HS_ERR_INVALID_ARG; }
-        if (d.forms < 1 || d.forms > 3) { delete p; return HS_ERR_INVALID_ARG; }
+        if (d.forms < 1 || d.forms > 7) { delete p; return HS_ERR_INVALID_ARG; }
         if (d.num_spectra < 1 || d.num_spectra > (int64_t(1) << 30) || !d.lengths) { delete p; return HS_ERR_INVALID_ARG; }
         const int64_t B = d.num_spectra;
         const int eb = elem_bytes(d.dtype);
@@ -626,6 +712,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         p->len.assign(d.lengths, d.lengths + B);
         p->in_off.assign(B + 1, 0);
         p->nf.assign(B, 0);
+        p->nf_main.assign(B, 0);
         p->fund_off.assign(B + 1, 0);
         int64_t pos = 0;
         for (int64_t s = 0; s < B; ++s) {
@@ -641,7 +728,9 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
             p->in_off[s] = off;
             pos = off + n;
             p->extent = std::max(p->extent, off + n);
-            p->nf[s] = (n - 1) / d.H;
+            p->nf_main[s] = (n - 1) / d.H;
+            // with the truncated tail every n < N - 1 is a fundamental (its order 1 fits)
+            p->nf[s] = (d.flags & HS_FLAG_TRUNCATE_TAIL) ? n - 1 : p->nf_main[s];
             p->fund_off[s + 1] = p->fund_off[s] + p->nf[s];
             p->max_len = std::max(p->max_len, n);
         }
@@ -662,7 +751,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         if (d.H < 1 || d.H > kMaxH2D || d.forms != HS_FORM_GREEDY) { delete p; return HS_ERR_INVALID_ARG; }
         if (d.dtype != HS_F32) { delete p; return HS_ERR_UNSUPPORTED; }
         if (d.num_spectra != 1) { delete p; return HS_ERR_INVALID_ARG; }
-        if (d.flags & (HS_FLAG_WHITENING | HS_FLAG_PER_SPECTRUM_NORM)) { delete p; return HS_ERR_UNSUPPORTED; }
+        if (d.flags & (HS_FLAG_WHITENING | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_TRUNCATE_TAIL)) { delete p; return HS_ERR_UNSUPPORTED; }
         if (d.n_freq < 3 || d.n_rows < 3 || d.z0_row < 0 || d.z0_row >= d.n_rows) { delete p; return HS_ERR_INVALID_ARG; }
         if (d.n_freq > (int64_t(1) << 36) || d.n_rows > (int64_t(1) << 20)) { delete p; return HS_ERR_INVALID_ARG; }
         const int64_t H = d.H;
@@ -688,6 +777,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         p->in_off.assign(2, 0);
         p->in_off[1] = p->extent;
         p->nf.assign(1, p->total_fund);
+        p->nf_main.assign(1, p->total_fund);
         p->fund_off = {0, p->total_fund};
         p->max_len = p->extent;
     } else {
@@ -704,10 +794,17 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
     if (!guard.ok) { delete p; return HS_ERR_CUDA; }
     if (!cuda_ok(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, device)) ||
         !cuda_ok(cudaDeviceGetAttribute(&p->l2_bytes, cudaDevAttrL2CacheSize, device))) { delete p; return HS_ERR_CUDA; }
+    if (d.dims == 1) {
+        // the default launch shape depends on whether the input fits in this device's L2
+        p->tun = default_tuning(p);
+        compute_tiles(p);
+    }
     const size_t B1 = p->in_off.size();
     if (!cuda_ok(cudaMalloc(&p->d_in_off, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_fund_off, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_tile_start, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_tail_tile_start, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_nf_main, sizeof(int64_t) * (B1 - 1))) ||
         !cuda_ok(cudaMalloc(&p->d_in_len, sizeof(int64_t) * (B1 - 1))) ||
         !cuda_ok(cudaMalloc(&p->d_err, sizeof(int)))) {
         free_plan(p);
@@ -716,12 +813,15 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
     if (!cuda_ok(cudaMemcpy(p->d_in_off, p->in_off.data(), sizeof(int64_t) * B1, cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemcpy(p->d_fund_off, p->fund_off.data(), sizeof(int64_t) * B1, cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemcpy(p->d_in_len, p->len.data(), sizeof(int64_t) * (B1 - 1), cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemcpy(p->d_nf_main, p->nf_main.data(), sizeof(int64_t) * (B1 - 1), cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemcpy(p->d_tail_tile_start, p->tail_tile_start.data(), sizeof(int64_t) * B1,
+                            cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemset(p->d_err, 0, sizeof(int)))) {
         free_plan(p);
         return HS_ERR_CUDA;
     }
     hs_status st = upload_tiles(p);
-    if (st == HS_OK && d.dims == 1 && (d.flags & HS_FLAG_AUTOTUNE)) st = autotune(p);
+    if (st == HS_OK && d.dims == 1 && (d.flags & HS_FLAG_AUTOTUNE) && (d.forms & 3)) st = autotune(p);
     if (st != HS_OK) {
         free_plan(p);
         return st;
@@ -856,6 +956,55 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
     return HS_OK;
 }
 
+hs_status hs_run_optimal(hs_plan p, const void *spectra, const float *w, const hs_form_io *optimal, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    if (p->d.dims != 1 || !(p->d.forms & HS_FORM_OPTIMAL)) return HS_ERR_INVALID_ARG;
+    if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
+    if (w && !aligned(w, 16)) return HS_ERR_INVALID_ARG;
+    {
+        hs_status cs = check_io(p, optimal, true);
+        if (cs != HS_OK) return cs;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    const int64_t B = p->d.num_spectra;
+    if (optimal->argmax) HS_CUDA(cudaMemsetAsync(optimal->argmax, 0, sizeof(uint64_t) * B, st));
+    Fwd1DArgs a{};
+    a.x = spectra;
+    a.w = w;
+    a.in_off = p->d_in_off;
+    a.fund_off = p->d_fund_off;
+    a.in_len = p->d_in_len;
+    a.nf_main = p->d_nf_main;
+    a.B = static_cast<int32_t>(B);
+    a.H = p->d.H;
+    a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;
+    a.per_spectrum_norm = (p->d.flags & HS_FLAG_PER_SPECTRUM_NORM) ? 1 : 0;
+    a.path_bytes = p->path_bytes;
+    a.checked = (p->d.flags & HS_FLAG_CHECKED) ? 1 : 0;
+    a.err = p->d_err;
+    FormArgs o = to_form_args(optimal);
+    // one warp per fundamental; each warp takes a contiguous run of fundamentals
+    const int threads = 256, wpc = threads / 32;
+    int64_t F = p->total_fund;
+    const void *fn = fwd1d_opt_kernel(p->d.dtype, whiten ? 1 : 0);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    int occ = 0;
+    HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));
+    // one wave of resident CTAs
+    const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((F + wpc - 1) / wpc,
+                                                                static_cast<int64_t>(p->sms) * std::max(occ, 1)));
+    int64_t chunk = (F + ctas * wpc - 1) / (ctas * wpc);
+    void *args[] = {&a, &o, &F, &chunk};
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(ctas)), dim3(threads), args, 0, st));
+    return HS_OK;
+}
+
 hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_form_io *fwd,
                       const void *spectra, const float *w, float *grad_in, float *grad_w,
                       void *workspace, void *stream)
@@ -863,10 +1012,12 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
     if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
-    if (form != HS_FORM_SIMPLE && form != HS_FORM_GREEDY) return HS_ERR_INVALID_ARG;
+    if (form != HS_FORM_SIMPLE && form != HS_FORM_GREEDY && form != HS_FORM_OPTIMAL) return HS_ERR_INVALID_ARG;
     if (!(p->d.forms & form)) return HS_ERR_INVALID_ARG;
     if (!grad_snr || !fwd || !fwd->best_h || !fwd->sigma) return HS_ERR_INVALID_ARG;
-    if (form == HS_FORM_GREEDY && !fwd->path) return HS_ERR_INVALID_ARG;
+    if (form != HS_FORM_SIMPLE && !fwd->path) return HS_ERR_INVALID_ARG;
+    // the optimal form's bins follow its recorded drift path exactly as the greedy form's do
+    const int kform = form == HS_FORM_SIMPLE ? HS_FORM_SIMPLE : HS_FORM_GREEDY;
     if (!aligned(grad_snr, 4) || !aligned(fwd->sigma, 4)) return HS_ERR_INVALID_ARG;
     if (fwd->path && !aligned(fwd->path, p->path_bytes)) return HS_ERR_INVALID_ARG;
     const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
@@ -877,7 +1028,7 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     if ((grad_in && !aligned(grad_in, 4)) || (grad_w && !aligned(grad_w, 4))) return HS_ERR_INVALID_ARG;
     const int64_t B = p->d.num_spectra;
     Bwd1DArgs a{};
-    a.form = form;
+    a.form = kform;
     a.H = p->d.H;
     a.B = static_cast<int32_t>(B);
     a.path_bytes = p->path_bytes;
@@ -922,7 +1073,7 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     if (gx > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     a.blocks_per_spectrum = gx;
     if (workspace && !aligned(workspace, 16)) return HS_ERR_INVALID_ARG;
-    const void *fn = bwd1d_kernel(form, p->d.dtype, whiten ? 1 : 0);
+    const void *fn = bwd1d_kernel(kform, p->d.dtype, whiten ? 1 : 0);
     if (!fn) return HS_ERR_UNSUPPORTED;
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
@@ -939,7 +1090,7 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
         int64_t F = p->total_fund;
         void *margs[] = {&a, &F};
         const unsigned mgrid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((F + 255) / 256, 16 * p->sms)));
-        HS_CUDA(cudaLaunchKernel(bwd_mark_kernel(form), dim3(mgrid), dim3(256), margs, 0, st));
+        HS_CUDA(cudaLaunchKernel(bwd_mark_kernel(kform), dim3(mgrid), dim3(256), margs, 0, st));
     }
     void *args[] = {&a};
     const size_t smem = kBwdBlockBins * sizeof(long long) + max_cand * (sizeof(float) + sizeof(int16_t));

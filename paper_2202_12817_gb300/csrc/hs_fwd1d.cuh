@@ -99,6 +99,24 @@ __device__ __forceinline__ void block_argmax(unsigned long long key, unsigned lo
     }
 }
 
+// Next-spectrum L2 prefetch: tile i of the T_s tiles of spectrum s brings share i of spectrum
+// s+1's input bytes into L2 (cp.async.bulk.prefetch, 16-byte units), so that when spectrum s+1's
+// tiles start, their dependent chains of gathers hit L2 instead of DRAM.
+__device__ __forceinline__ void prefetch_next_spectrum(const Fwd1DArgs &a, int s, int64_t tile)
+{
+    if (!a.pf_next || threadIdx.x != 0 || s + 1 >= a.B) return;
+    const int64_t t0 = __ldg(a.tile_start + s), nt = __ldg(a.tile_start + s + 1) - t0;
+    const int64_t nb = __ldg(a.in_len + s + 1) * a.elem_bytes;
+    const int64_t chunk = ((nb + nt - 1) / nt + 15) & ~static_cast<int64_t>(15);
+    int64_t lo = (tile - t0) * chunk;
+    const int64_t hi = lo + chunk < nb ? lo + chunk : nb;
+    const unsigned char *src = static_cast<const unsigned char *>(a.x) + __ldg(a.in_off + s + 1) * a.elem_bytes;
+    for (; lo + 16 <= hi; lo += 65536) {
+        const int64_t b = (hi - lo < 65536 ? hi - lo : 65536) & ~static_cast<int64_t>(15);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + lo), "r"(static_cast<uint32_t>(b)) : "memory");
+    }
+}
+
 // spectrum owning a tile: largest s with tile_start[s] <= t
 __device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t)
 {
@@ -185,6 +203,7 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
     }
     while (tile < a.total_tiles) {
         const int s = tile_spectrum(a.tile_start, a.B, tile);
+        prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
             loaded_spec = s;
         }
         const int64_t fbase = __ldg(a.fund_off + s);
-        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t nf = __ldg(a.nf_main + s);
         const int64_t n = (tile - __ldg(a.tile_start + s)) * blockDim.x + threadIdx.x;
         const bool valid = n < nf;
         const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
@@ -332,6 +351,7 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
     int loaded_spec = -1;
     for (int64_t tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
         const int s = tile_spectrum(a.tile_start, a.B, tile);
+        prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
@@ -341,7 +361,7 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
             loaded_spec = s;
         }
         const int64_t fbase = __ldg(a.fund_off + s);
-        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t nf = __ldg(a.nf_main + s);
         const int64_t n0 = (tile - __ldg(a.tile_start + s)) * (F * blockDim.x) + threadIdx.x;
         const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
         const float *wv = a.w;
@@ -428,6 +448,106 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
         }
         if (tile + gridDim.x < a.total_tiles) __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// kernel: the truncated tail (HS_FLAG_TRUNCATE_TAIL), fundamentals N_f <= n < N - 1 whose
+// higher orders would read past the end of the spectrum.  Each form keeps the orders whose
+// every possible read fits: simple h n <= N - 1, greedy h n + h <= N - 1 (drift at most h - 1
+// after order h - 1, plus the compared neighbour).  One thread per fundamental, both forms, a
+// CTA per 256 consecutive tail fundamentals of one spectrum.
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
+{
+    __shared__ NormSmem nm;
+    __shared__ unsigned long long red[32];
+    constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
+    constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
+    const int H = a.H;
+    const int64_t tile = blockIdx.x;
+    const int s = tile_spectrum(a.tail_tile_start, a.B, tile);
+    const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
+    if (kS) load_norm(nm, 0, a.s.mu + no, a.s.sigma + no, H);
+    if (kG) load_norm(nm, 1, a.g.mu + no, a.g.sigma + no, H);
+    __syncthreads();
+    const int64_t fbase = __ldg(a.fund_off + s);
+    const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1
+    const int64_t len = __ldg(a.in_len + s);
+    const int64_t n = __ldg(a.nf_main + s) + (tile - __ldg(a.tail_tile_start + s)) * blockDim.x + threadIdx.x;
+    const bool valid = n < nf;
+    const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
+    const float *wv = a.w;
+    RunMax ms{0.f, 1}, mg{0.f, 1};
+    uint32_t bits = 0;
+    if (valid) {
+        // orders of each form (n >= N_f >= 1 here); 2 <= ... reads stay below N
+        const int64_t hs_ = (len - 1) / n, hg_ = (len - 1) / (n + 1);
+        const int Hs = static_cast<int>(hs_ < H ? hs_ : H), Hg = static_cast<int>(hg_ < H ? hg_ : H);
+        const uint32_t n32 = static_cast<uint32_t>(n);
+        const float x0 = ld_x<T, WHITEN>(x, wv, n32);
+        float ss = x0, sg = x0;
+        uint32_t d = 0;
+        if (kG && a.mitigation) {
+            const float b = ld_x<T, WHITEN>(x, wv, n32 + 1);
+            if (b > x0) { d = 1; sg = b; bits = 1u; }
+        }
+        if (kS) ms.first(fmaf(ss, nm.rs[0][0], -nm.murs[0][0]));
+        if (kG) mg.first(fmaf(sg, nm.rs[1][0], -nm.murs[1][0]));
+        const int Hmax = (kS && kG) ? (Hs > Hg ? Hs : Hg) : (kS ? Hs : Hg);
+        uint32_t hn = n32;
+        for (int h = 2; h <= Hmax; ++h) {
+            hn += n32;
+            if (kS && h <= Hs) {
+                ss += ld_x<T, WHITEN>(x, wv, hn);
+                ms.step(fmaf(ss, nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
+            }
+            if (kG && h <= Hg) {
+                const uint32_t m = hn + d;
+                const float va = ld_x<T, WHITEN>(x, wv, m);
+                const float vb = ld_x<T, WHITEN>(x, wv, m + 1);
+                const bool inc = vb > va;
+                sg += inc ? vb : va;
+                d += inc;
+                bits |= static_cast<uint32_t>(inc) << (h - 1);
+                mg.step(fmaf(sg, nm.rs[1][h - 1], -nm.murs[1][h - 1]), h);
+            }
+        }
+        const int64_t o = fbase + n;
+        if (kS) {
+            a.s.snr[o] = ms.best;
+            a.s.best_h[o] = static_cast<uint8_t>(ms.bh);
+        }
+        if (kG) {
+            a.g.snr[o] = mg.best;
+            a.g.best_h[o] = static_cast<uint8_t>(mg.bh);
+            if (a.g.path) store_path(a.g.path, a.path_bytes, o, bits);
+        }
+    }
+    if (kS && a.s.argmax) block_argmax(valid ? argmax_key(ms.best, n) : 0ull, a.s.argmax + s, red);
+    if (kG && a.g.argmax) {
+        if (kS && a.s.argmax) __syncthreads();
+        block_argmax(valid ? argmax_key(mg.best, n) : 0ull, a.g.argmax + s, red);
+    }
+}
+
+template <typename T>
+static const void *fwd1d_tail_kernel_for(int forms, int whitening)
+{
+    if (whitening) {
+        switch (forms) {
+        case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, true>);
+        case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 2, true>);
+        case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 3, true>);
+        }
+    } else {
+        switch (forms) {
+        case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, false>);
+        case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 2, false>);
+        case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 3, false>);
+        }
+    }
+    return nullptr;
 }
 
 // ---------------------------------------------------------------------------------------

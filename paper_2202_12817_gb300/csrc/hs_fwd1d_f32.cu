@@ -8,4 +8,8 @@ const void *fwd1d_kernel_f32(int forms, int whitening, int kernel)
 {
     return fwd1d_kernel_for<float>(forms, whitening, kernel);
 }
+const void *fwd1d_tail_kernel_f32(int forms, int whitening)
+{
+    return fwd1d_tail_kernel_for<float>(forms, whitening);
+}
 }  // namespace hs

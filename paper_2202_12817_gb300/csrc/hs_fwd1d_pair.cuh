@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
     }
     while (tile < a.total_tiles) {
         const int s = tile_spectrum(a.tile_start, a.B, tile);
+        prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
             loaded_spec = s;
         }
         const int64_t fbase = __ldg(a.fund_off + s);
-        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t nf = __ldg(a.nf_main + s);
         const int64_t n0 = (tile - __ldg(a.tile_start + s)) * (CH * fpp) + li;
         const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
         const float *wv = a.w;

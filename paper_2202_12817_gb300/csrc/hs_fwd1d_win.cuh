@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(640) k_fwd1d_win(const Fwd1DArgs a, const WinP
             if (s_abort) { ok = false; break; }
             const int64_t tile = blockIdx.x + k * gridDim.x;
             const int s = tile_spectrum(a.tile_start, a.B, tile);
-            const int64_t nf = __ldg(a.fund_off + s + 1) - __ldg(a.fund_off + s);
+            const int64_t nf = __ldg(a.nf_main + s);
             const int64_t n0 = (tile - __ldg(a.tile_start + s)) * Tn;
             const int64_t n_last = (n0 + Tn < nf ? n0 + Tn : nf) - 1;
             const int64_t base = __ldg(a.in_off + s);
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(640) k_fwd1d_win(const Fwd1DArgs a, const WinP
             loaded_spec = s;
         }
         const int64_t fbase = __ldg(a.fund_off + s);
-        const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;
+        const int64_t nf = __ldg(a.nf_main + s);
         const int64_t n = (tile - __ldg(a.tile_start + s)) * Tn + t;
         const bool valid = n < nf;
         float best_s = 0.f, best_g = 0.f;

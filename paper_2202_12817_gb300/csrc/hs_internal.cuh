@@ -36,7 +36,10 @@ struct Fwd1DArgs {
     const void *x;                 // concatenated spectra (dtype of the plan)
     const float *w;                // whitening weights [N] or nullptr
     const int64_t *in_off;         // [B+1] element offset of each spectrum
-    const int64_t *fund_off;       // [B+1] output offset of each spectrum (prefix of N_f)
+    const int64_t *fund_off;       // [B+1] output offset of each spectrum (prefix of its fundamentals)
+    const int64_t *nf_main;        // [B] fundamentals with all H orders, N_f = floor((N-1)/H)
+    const int64_t *tail_tile_start;// [B+1] prefix of truncated-tail tiles (HS_FLAG_TRUNCATE_TAIL)
+    int64_t tail_tiles;            // total truncated-tail tiles (0 without the flag)
     const int64_t *tile_start;     // [B+1] prefix of tiles per spectrum
     const int64_t *in_len;         // [B] N_s (for checked mode)
     int32_t B;
@@ -51,6 +54,8 @@ struct Fwd1DArgs {
     int64_t extent;                // readable elements of the input buffer (vector loads stay below)
     int64_t pf_chunk;              // > 0: CTA i first prefetches input bytes [i c, (i+1) c) into L2
     int64_t pf_bytes;              // input bytes covered by that prefetch
+    int32_t pf_next;               // 1: the tiles of spectrum s prefetch spectrum s+1 into L2, one share each
+    int32_t elem_bytes;            // bytes per stored element
     FormArgs s;                    // simple form outputs (unused unless the form is on)
     FormArgs g;                    // greedy form outputs
     int *err;                      // device error word
@@ -132,6 +137,12 @@ const void *fwd1d_kernel_f32(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel();
+const void *fwd1d_opt_kernel(int dtype, int whitening);
+// 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 per CTA
+const void *fwd1d_tail_kernel_f32(int forms, int whitening);
+const void *fwd1d_tail_kernel_f16(int forms, int whitening);
+const void *fwd1d_tail_kernel_bf16(int forms, int whitening);
+constexpr int kTailThreads = 256;
 const void *bwd1d_kernel(int form, int dtype, int whitening);
 const void *bwd_dw_reduce_kernel();
 const void *bwd_mark_kernel(int form);

@@ -52,6 +52,9 @@ def test_norm_exponential_matches_oracle(hs, oracle_lib, form, dims, mit, mean1)
 def test_norm_exponential_rejects(hs):
     with pytest.raises(hs.HSError):
         hs.norm_exponential(1, 2, 8)          # 2D has only the greedy form
+    with pytest.raises(hs.HSError) as e:
+        hs.norm_exponential(hs.OPTIMAL, 1, 8)  # the optimum over paths has no closed form
+    assert e.value.status == 2
     with pytest.raises(hs.HSError):
         hs.norm_exponential(2, 1, 33)
     with pytest.raises(hs.HSError):
@@ -94,7 +97,8 @@ def test_plan_2d_domain_matches_oracle(hs, oracle_lib):
     dict(H=0, forms=3, lengths=[100]),
     dict(H=33, forms=3, lengths=[100]),
     dict(H=8, forms=0, lengths=[100]),
-    dict(H=8, forms=4, lengths=[100]),
+    dict(H=8, forms=8, lengths=[100]),
+    dict(H=4, forms=6, dims=2, n_freq=1000, n_rows=41, z0_row=20),   # 2D has no optimal form
     dict(H=8, forms=3, lengths=[8]),                       # N < H + 1: no fundamental
     dict(H=8, forms=3, lengths=[100], dtype=3),
     dict(H=8, forms=3, lengths=[100, 100], offsets=[0, 3]),   # misaligned offset

@@ -101,7 +101,11 @@ TUNINGS = [dict(kernel=0, threads=256),
            dict(kernel=7, threads=64, ctas_per_sm=6, dynamic=1, prefetch=1),
            dict(kernel=7, threads=256, ctas_per_sm=2),
            dict(kernel=7, threads=128, ctas_per_sm=16, prefetch=1),
-           dict(kernel=6, threads=192, ctas_per_sm=3, dynamic=1)]
+           dict(kernel=6, threads=192, ctas_per_sm=3, dynamic=1),
+           dict(kernel=3, threads=128, fund_per_thread=2, prefetch=2),
+           dict(kernel=0, threads=256, prefetch=2),
+           dict(kernel=6, threads=128, prefetch=3),
+           dict(kernel=7, threads=64, ctas_per_sm=8, prefetch=2)]
 # one launch shape per kernel id, for the tests that sweep ids
 BY_KERNEL = {1: TUNINGS[1], 2: TUNINGS[5], 3: TUNINGS[10], 6: TUNINGS[14], 7: TUNINGS[16]}
 
@@ -158,7 +162,8 @@ def test_small_and_degenerate_lengths(hs, oracle_lib):
 def test_uneven_batch_per_spectrum_norm(hs, oracle_lib):
     b = synth.uneven_batch(count=24, seed=77, choices=(1 << 12, 1 << 13, 1 << 15, 1 << 17), pulsar_fraction=0.25)
     xs = [synth.batch_trial(b, i) for i in range(24)]
-    for t in (TUNINGS[1], TUNINGS[4], TUNINGS[5], TUNINGS[8], TUNINGS[15], TUNINGS[16]):
+    for t in (TUNINGS[1], TUNINGS[4], TUNINGS[5], TUNINGS[8], TUNINGS[15], TUNINGS[16], TUNINGS[20],
+              TUNINGS[21], TUNINGS[22], TUNINGS[23]):
         run_case(hs, oracle_lib, xs, 16, per_spec_norm=True, tuning=t)
         run_case(hs, oracle_lib, xs, 16, dtype=1, tuning=t)
 

@@ -234,6 +234,115 @@ def test_brute_force_bounds_and_reproduces_greedy(oracle_lib, mitigation, seed):
             assert np.all(allv[n] <= best + 1e-12)
 
 
+@pytest.mark.parametrize("mitigation", [True, False])
+def test_optimal_form_is_the_brute_force_optimum(oracle_lib, mitigation):
+    """optimal_1d's every-order sums are the exhaustive maxima over drift paths (tiny inputs),
+    bound the greedy and simple sums from above, and its best h follows Eq. 2's maximum rule."""
+    o = oracle_lib
+    N, H = 96, 7
+    for seed in (4, 5):
+        x = synth.exp_noise(N, seed)
+        _, _, opt_all = o.optimal_1d(x, H, *unit_norm(H), mitigation=mitigation, want_all=True)
+        g_all = o.greedy_1d(x, H, *unit_norm(H), mitigation=mitigation, want_all=True)[3]
+        s_all = o.simple_1d(x, H, *unit_norm(H), want_all=True)[2]
+        for n in range(o.nf_1d(N, H)):
+            best = o.brute_1d(x, H, n, mitigation=mitigation)[0]
+            np.testing.assert_allclose(opt_all[n], best, rtol=0, atol=1e-12)
+        assert np.all(opt_all >= g_all - 1e-12) and np.all(opt_all >= s_all - 1e-12)
+        mu = np.linspace(0.5, 4.0, H)
+        sg = np.linspace(1.0, 2.5, H)
+        snr, bh, allv = o.optimal_1d(x, H, mu, sg, mitigation=mitigation, want_all=True)
+        for n in range(allv.shape[0]):
+            v = allv[n]
+            h = 0
+            for k in range(1, H):
+                if v[k] > v[h]:
+                    h = k
+            assert bh[n] == h + 1 and snr[n] == v[h]
+            np.testing.assert_allclose(v, (opt_all[n] - mu) / sg, rtol=1e-12)
+
+
+def test_optimal_form_special_cases(oracle_lib):
+    """H = 1 with mitigation: max(x[n], x[n+1]); an increasing spectrum: every increment (the
+    greedy path is then optimal); the noise-free pulse train: the optimum collects every harmonic
+    peak, as the greedy does (41.135167 at H = 32, n = 1234)."""
+    o = oracle_lib
+    x = synth.exp_noise(1000, 9)
+    s1 = o.optimal_1d(x, 1, *unit_norm(1), want_all=True)[2][:, 0]
+    np.testing.assert_array_equal(s1, np.maximum(x[:-1], x[1:]).astype(np.float64)[:s1.size])
+    s1u = o.optimal_1d(x, 1, *unit_norm(1), mitigation=False, want_all=True)[2][:, 0]
+    np.testing.assert_array_equal(s1u, x[:s1u.size].astype(np.float64))
+    inc = np.arange(1, 801, dtype=np.float32)
+    H = 8
+    g = o.greedy_1d(inc, H, *unit_norm(H), want_all=True)[3]
+    opt = o.optimal_1d(inc, H, *unit_norm(H), want_all=True)[2]
+    np.testing.assert_array_equal(opt, g)
+    gold = json.load(open(os.path.join(GOLD, "pulse_train_1234.json")))
+    H, n = gold["H"], gold["fundamental_bin"]
+    pul = synth.Pulsar(gold["f0_bins"], gold["duty"], gold["amplitude"])
+    xp = synth.inject(np.zeros(synth.CONFIG1_N, np.float32), [pul])
+    opt = o.optimal_1d(xp, H, *unit_norm(H), nf=n + 1, want_all=True)[2]
+    assert abs(opt[n, -1] - 41.13516668) < 1e-4
+
+
+@pytest.mark.parametrize("mitigation", [True, False])
+def test_tail_reduces_to_full_forms_where_they_fit(oracle_lib, mitigation):
+    """Below N_f every order fits, so the truncated-tail rule gives the full forms exactly."""
+    o = oracle_lib
+    N, H = 3001, 16
+    x = synth.exp_noise(N, 12)
+    nf = o.nf_1d(N, H)
+    mu, sg = np.linspace(1.0, 9.0, H), np.linspace(1.0, 3.0, H)
+    s, b = o.simple_1d(x, H, mu, sg)
+    g, gb, gp = o.greedy_1d(x, H, mu, sg, mitigation=mitigation)
+    q, qb = o.optimal_1d(x, H, mu, sg, mitigation=mitigation)
+    ts, tb, _ = o.tail_1d(1, x, H, mu, sg, lo=0, hi=nf)
+    tg, tgb, tgp = o.tail_1d(2, x, H, mu, sg, mitigation=mitigation, lo=0, hi=nf)
+    tq, tqb, _ = o.tail_1d(4, x, H, mu, sg, mitigation=mitigation, lo=0, hi=nf)
+    np.testing.assert_array_equal(ts, s), np.testing.assert_array_equal(tb, b)
+    np.testing.assert_array_equal(tg, g), np.testing.assert_array_equal(tgb, gb)
+    np.testing.assert_array_equal(tgp, gp)
+    np.testing.assert_array_equal(tq, q), np.testing.assert_array_equal(tqb, qb)
+
+
+def test_tail_order_counts_are_the_largest_that_fit(oracle_lib):
+    """On a strictly increasing spectrum the greedy increments at every order, so its last bin
+    is H_n n + H_n: inside the spectrum, while one more order would leave it; the simple form's
+    last bin H_n n likewise."""
+    o = oracle_lib
+    N, H = 2000, 32
+    x = np.arange(1, N + 1, dtype=np.float32)
+    lo = o.nf_1d(N, H)
+    _, gb, gp, gall = o.tail_1d(2, x, H, *unit_norm(H), want_all=True)
+    _, sb, _, sall = o.tail_1d(1, x, H, *unit_norm(H), want_all=True)
+    for i, n in enumerate(range(lo, N - 1)):
+        hg = int(np.sum(~np.isnan(gall[i])))
+        assert hg == o.tail_orders(2, N, H, n)
+        assert hg * n + hg <= N - 1 and (hg + 1) * (n + 1) > N - 1 or hg == H
+        assert gp[i] == (1 << hg) - 1 and gb[i] == hg       # increasing: every increment, last order best
+        hs_ = int(np.sum(~np.isnan(sall[i])))
+        assert hs_ * n <= N - 1 and ((hs_ + 1) * n > N - 1 or hs_ == H)
+        assert sb[i] == hs_
+
+
+def test_tail_pulse_train(oracle_lib):
+    """A noise-free pulse train whose fundamental lies past N_f: at n = 200 of a 4096-bin
+    spectrum (N_f = 127 at H = 32) the greedy, simple and optimal forms all keep
+    floor(4095 / 201) = 20 and floor(4095 / 200) = 20 orders, and each sums the first 20
+    harmonic powers 8 exp(-(pi 0.05 k)^2)."""
+    o = oracle_lib
+    N, H, n = 4096, 32, 200
+    x = synth.inject(np.zeros(N, np.float32), [synth.Pulsar(200.0, 0.05, 8.0)])
+    k = np.arange(1, 21)
+    want = np.sum(np.float32(8.0 * np.exp(-(np.pi * 0.05 * k) ** 2)).astype(np.float64))
+    lo = o.nf_1d(N, H)
+    assert lo == 127
+    for form in (1, 2, 4):
+        _, b, _, allv = o.tail_1d(form, x, H, *unit_norm(H), lo=n, hi=n + 1, want_all=True)
+        assert int(np.sum(~np.isnan(allv[0]))) == 20
+        assert abs(allv[0, 19] - want) < 1e-9 and b[0] == 20
+
+
 def test_path_invariants(oracle_lib):
     """d_m(h) = h-1 between fundamentals (Sec. 2.2); the fundamental comparison adds at most 1."""
     o = oracle_lib
