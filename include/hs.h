@@ -160,6 +160,9 @@ hs_status hs_plan_domain_2d(hs_plan plan, int64_t *f_lo, int64_t *f_hi, int64_t 
  * (up to 16 groups; required for a whitening plan with grad_w) followed by one byte per
  * (spectrum, 1024-bin block) that marks the blocks receiving contributions. */
 hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
+/* Launch shape of the forward.  2D plans take only kernel 0 (CTAs over f-tiles fastest) or 1 (over
+ * z rows fastest, the default: neighbouring z, whose low orders read overlapping rows, stay
+ * co-resident), with threads = 256 and every other field 0. */
 hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
 hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 

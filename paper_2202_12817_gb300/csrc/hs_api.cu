@@ -349,7 +349,11 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         a.g = to_form_args(greedy);
         a.err = p->d_err;
         const int threads = 256;
-        dim3 grid(static_cast<unsigned>((a.nff + threads - 1) / threads), static_cast<unsigned>(a.nz));
+        const int64_t ftiles = (a.nff + threads - 1) / threads;
+        // tuning.kernel 1 (2D): z rows fastest, while the f-tiles fit in grid.y
+        a.zfast = (p->tun.kernel == 1 && ftiles <= 65535) ? 1 : 0;
+        dim3 grid = a.zfast ? dim3(static_cast<unsigned>(a.nz), static_cast<unsigned>(ftiles))
+                            : dim3(static_cast<unsigned>(ftiles), static_cast<unsigned>(a.nz));
         void *args[] = {&a};
         HS_CUDA(cudaLaunchKernel(fwd2d_kernel(), grid, dim3(threads), args, 0, st));
         return HS_OK;
@@ -773,6 +777,8 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         p->total_fund = (p->f_hi - p->f_lo + 1) * (p->z_hi - p->z_lo + 1);
         p->extent = d.n_freq * d.n_rows;
         p->path_bytes = 4;
+        // z rows fastest: 0.632 ms vs 0.674 ms (f-tiles fastest) on the 201 x 2^21 plane, H = 8
+        p->tun = hs_tuning{1, 256, 1, 0, 0, 0, 0, 0, 0};
         p->len.assign(1, p->extent);
         p->in_off.assign(2, 0);
         p->in_off[1] = p->extent;
@@ -879,6 +885,16 @@ hs_status hs_plan_get_tuning(hs_plan p, hs_tuning *t)
 hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
 {
     if (!p) return HS_ERR_INVALID_ARG;
+    if (p->d.dims == 2) {
+        // 2D: kernel 0 = f-tiles fastest, 1 = z rows fastest; 256 threads, nothing else
+        if (!t || (t->kernel != 0 && t->kernel != 1) || t->threads != 256 || t->fund_per_thread != 1 ||
+            t->ctas_per_sm || t->dynamic || t->stages || t->stage_kb || t->prefetch || t->producers)
+            return HS_ERR_INVALID_ARG;
+        std::lock_guard<std::mutex> lk(p->mu);
+        p->tun = *t;
+        p->gvalid = false;
+        return HS_OK;
+    }
     if (p->d.dims != 1) return HS_ERR_UNSUPPORTED;
     hs_status st = validate_tuning(p, t);
     if (st != HS_OK) return st;

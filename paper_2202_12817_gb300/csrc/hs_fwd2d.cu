@@ -18,8 +18,11 @@ __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
         murs[threadIdx.x] = __fmul_rn(__ldg(a.g.mu + threadIdx.x), r);
     }
     __syncthreads();
-    const int64_t fi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t zi = blockIdx.y;
+    // block order: f-tiles fastest (grid.x = f-tile), or z rows fastest (grid.x = z), which keeps
+    // the fundamentals of neighbouring z -- whose low orders read overlapping rows -- co-resident
+    const int64_t ft = a.zfast ? blockIdx.y : blockIdx.x;
+    const int64_t fi = ft * blockDim.x + threadIdx.x;
+    const int64_t zi = a.zfast ? blockIdx.x : blockIdx.y;
     const bool valid = fi < a.nff;
     const int64_t o = zi * a.nff + fi;
     float best = 0.f;

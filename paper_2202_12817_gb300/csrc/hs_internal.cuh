@@ -94,6 +94,7 @@ struct Fwd2DArgs {
     int64_t f_lo, nff;             // f in [f_lo, f_lo + nff)
     int64_t z_lo, nz;              // z in [z_lo, z_lo + nz)
     int32_t checked;
+    int32_t zfast;                 // 1: grid.x runs over z, grid.y over f-tiles
     FormArgs g;
     int *err;
 };

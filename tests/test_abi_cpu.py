@@ -196,3 +196,16 @@ def test_plan_create_without_gpu_fails_cleanly(hs):
     with pytest.raises(hs.HSError) as e:
         hs.Plan(H=8, forms=3, lengths=[100])
     assert e.value.status == 4
+
+
+def test_tuning_2d_block_order(hs):
+    """2D plans take only the block order: kernel 0 (f-tiles fastest) or 1 (z rows fastest, the
+    default) with 256 threads."""
+    p = hs.Plan(4, hs.GREEDY, dims=2, n_freq=1000, n_rows=41, z0_row=20, flags=hs.FLAG_NO_DEVICE)
+    assert p.tuning.kernel == 1 and p.tuning.threads == 256
+    p.tuning = dict(kernel=0, threads=256)
+    assert p.tuning.kernel == 0
+    for bad in (dict(kernel=2, threads=256), dict(kernel=1, threads=128), dict(kernel=1, threads=256, dynamic=1)):
+        with pytest.raises(hs.HSError):
+            p.tuning = bad
+    p.close()

@@ -13,9 +13,12 @@ DEV = torch.device("cuda", 0)
 # ---------------------------------------------------------------------------------------------
 # 2D greedy
 # ---------------------------------------------------------------------------------------------
-def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0):
+def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None):
     n_rows, n_freq = pl.shape
     plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=flags)
+    if order is not None:
+        plan.tuning = dict(kernel=order, threads=256)     # 0: f-tiles fastest, 1: z rows fastest
+        assert plan.tuning.kernel == order
     assert plan.domain == o.domain_2d(n_freq, n_rows, z0, H)
     mu, sg = hs.norm_exponential(2, 2, H, True, mean1)
     ng = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
@@ -31,11 +34,12 @@ def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0):
     return near
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("H", [1, 2, 3, 4, 8])
-def test_2d_small(hs, oracle_lib, H):
+def test_2d_small(hs, oracle_lib, H, order):
     z0 = 30
     pl = synth.plane(5003, 2 * z0 + 1, z0, 40 + H, synth.random_tracks(3, 5003, 8, f_lo=50, zmax=3))
-    run_2d(hs, oracle_lib, pl, z0, H)
+    run_2d(hs, oracle_lib, pl, z0, H, order=order)
 
 
 def test_2d_asymmetric_rows_checked(hs, oracle_lib):
@@ -52,8 +56,9 @@ def test_2d_full_size(hs, oracle_lib):
     """f-fdot plane 201 x 2^21, H = 8, chi-square(2) noise + 8 drifting tracks."""
     tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
     pl = synth.plane(synth.PLANE_N_FREQ, synth.PLANE_N_ROWS, synth.PLANE_Z0_ROW, synth.SEED_BASE + 4, tracks)
-    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8)
-    assert near <= 20
+    for order in (0, 1):
+        near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, order=order)
+        assert near <= 20
 
 
 # ---------------------------------------------------------------------------------------------
