@@ -178,7 +178,8 @@ hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_for
  * the SNR of S*_h (Eq. 2 with the caller's mu/sigma of the optimum), its maximum over h (first
  * strictly larger wins, as for the other forms), the best h and, if optimal->path is set, an
  * optimal drift path of that order (bit k-1 = increment at order k; ties keep the drift, and
- * the lowest final drift is taken among equal optima).  FP32 accumulation along each path.
+ * among the final drifts whose SNR equals the maximum the lowest is taken).  FP32 accumulation
+ * along each path.
  * Computed by a dynamic programme over the drift, one warp per fundamental.  Same input and
  * workspace-free; enqueued on `stream` without allocation or synchronisation. */
 hs_status hs_run_optimal(hs_plan plan, const void *spectra, const float *w, const hs_form_io *optimal,

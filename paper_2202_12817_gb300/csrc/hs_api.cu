@@ -584,6 +584,7 @@ hs_status autotune(hs_plan p)
                     t.ctas_per_sm = occ;
                     t.dynamic = sched == 2;
                 }
+                if (validate_tuning(sp, &t) != HS_OK) continue;
                 cands.push_back(t);
             }
     for (const hs_tuning &t : cands) {

@@ -1,22 +1,25 @@
 // Optimal partial sums of the 1D harmonic sum (HS_FORM_OPTIMAL): for every fundamental n and
 // order h, S*_h[n] = max over monotone drift paths of sum_{k<=h} x[k n + D_k], with
 // D_k - D_{k-1} in {0, 1}, D_0 = 0 and D_1 = 0 without scalloping-loss mitigation -- the
-// "optimal partial sum" over the bin choices the greedy form (Eq. 5 / Algorithm 2) makes
-// one order at a time (Sec. 2.2, Sec. 3).  The SNR, its maximum over h (Eq. 2) and the best h
+// best partial sum over the bin choices that the greedy form (Eq. 5 / Algorithm 2) makes one
+// order at a time (Sec. 2.2, Sec. 3).  The SNR, its maximum over h (Eq. 2) and the best h
 // follow as for the other forms; the path reported is an optimal path of the best h.
 //
 // Dynamic programme over the drift, one warp per fundamental: lane d holds
-//   best[h][d] = x[h n + d] + max(best[h-1][d], best[h-1][d-1]),
-// for d = 0..31 (lane 31 also holds d = 32, reachable only at order 32 with mitigation).
-// Each order's reads x[h n .. h n + h] are consecutive (one coalesced load) and do not depend
-// on the programme's state, so they are issued ahead of the arithmetic.  Ties keep the drift
-// (no increment), and among equal optima at the best h the lowest drift is reported.
+//   best[h][d] = x[h n + d] + max(best[h-1][d], best[h-1][d-1])
+// and the path that reaches it, for d = 0..31 (lane 31 also holds d = 32, reachable only at
+// order 32 with mitigation).  Each order's reads x[h n .. h n + h] are consecutive (one
+// coalesced load) and do not depend on the programme's state, so they are issued ahead of the
+// arithmetic.  Each lane keeps the running SNR maximum of its own state with its path; one warp
+// reduction at the end gives the best h and drift, whose lane holds the path.  Ties keep the
+// drift (no increment), and among the drifts whose SNR at the best h equals the maximum the
+// lowest is reported.
 #include "hs_fwd1d.cuh"
 
 namespace hs {
 
 template <typename T, bool WHITEN>
-__global__ void __launch_bounds__(256) k_fwd1d_opt(const Fwd1DArgs a, const FormArgs o, int64_t F, int64_t chunk)
+__global__ void __launch_bounds__(256, 4) k_fwd1d_opt(const Fwd1DArgs a, const FormArgs o, int64_t F, int64_t chunk)
 {
     __shared__ int tab_spec[8];           // spectrum whose table each warp last loaded
     __shared__ float2 wtab[8][kMaxH1D];   // per warp: (1/sigma, mu/sigma) of that spectrum
@@ -70,80 +73,94 @@ __global__ void __launch_bounds__(256) k_fwd1d_opt(const Fwd1DArgs a, const Form
             set_error(a.err, kErrBounds);
         const uint32_t n32 = static_cast<uint32_t>(n);
         const float *wv = a.w;
-        // order 1: drift 0, or 1 with mitigation
+        // Lane d holds the best sum ending at drift d and the path reaching it (bit k-1 set:
+        // increment at order k).  A state that no path reaches holds -inf: its bins are not
+        // read (the queue below holds -inf there), so no state needs a separate validity test.
+        // Order 1: drift 0, or drift 1 through the mitigation increment.
         const int dmax1 = mit ? 1 : 0;
+        const int lk = lane + 1 - dmax1;         // first order at which drift `lane` is reachable
         float best = lane <= dmax1 ? ld_x<T, WHITEN>(x, wv, n32 + lane) : NEG;
-        uint32_t bits = 0;                       // lane d: increments chosen into state d, bit h-1
-        float b32 = NEG;                         // lane 31: state d = 32 (order 32 with mitigation)
-        unsigned int cu = ordered_bits(best);
-        unsigned int m = __reduce_max_sync(0xffffffffu, cu);
-        uint32_t win = __ballot_sync(0xffffffffu, cu == m);
+        uint32_t pth = (mit && lane == 1) ? 1u : 0u;
+        // Each lane keeps the running maximum over h of its own state's SNR (first strictly larger
+        // wins) and the path that gave it; fl((S - mu)/sigma) = fma(S, rs, -murs) is monotone in
+        // S, so the maximum over lanes at the end is the maximum over h of the SNR of S*_h.
         float2 t = wtab[warp][0];
-        float bsnr = fmaf(__uint_as_float((m & 0x80000000u) ? (m & 0x7fffffffu) : ~m), t.x, -t.y);
-        int bh = 1, bd = __ffs(win) - 1;
-        int dmax = dmax1;
-        uint32_t hn = n32;
+        float lsnr = lane <= dmax1 ? fmaf(best, t.x, -t.y) : NEG;
+        int lh = 1, ld = lane;
+        uint32_t lpath = pth;
+        uint32_t bit = 1u;                       // 1 << (h - 1)
         // the values of the next PF orders, loaded ahead (the reads do not depend on the
-        // programme); lane d of order k reads x[k n + d] when drift d is reachable at order k
-        constexpr int PF = 4;
+        // programme): at the start of the block of orders h0 .. h0 + PF - 1, q[j] holds order
+        // h0 + j; lane d of order k reads x[k n + d] when drift d is reachable at order k
+        constexpr int PF = WHITEN ? 8 : 10;   // whitening keeps the registers for w
         float q[PF];
 #pragma unroll
         for (int j = 0; j < PF; ++j) {
-            const int k = 2 + j, dk = dmax1 + 1 + j;
-            q[j] = (k <= Hn && lane <= dk) ? ld_x<T, WHITEN>(x, wv, static_cast<uint32_t>(k) * n32 + lane) : NEG;
+            const int k = 2 + j;
+            q[j] = (k <= Hn && k >= lk) ? ld_x<T, WHITEN>(x, wv, static_cast<uint32_t>(k) * n32 + lane) : NEG;
         }
-        // drift 32 exists only at order 32 with mitigation: lane 31 loads it at the start
-        const float v32 = (Hn == 32 && mit && lane == 31) ? ld_x<T, WHITEN>(x, wv, 32u * n32 + 32u) : NEG;
-        for (int h = 2; h <= Hn; ++h) {
-            hn += n32;
-            const int dnew = dmax + 1;           // largest drift reachable at order h
-            const float v = q[0];
+        uint32_t kn = static_cast<uint32_t>(2 + PF) * n32;   // (order entering the queue) x n
+        // order h: best[h][d] = x[h n + d] + max(best[h-1][d], best[h-1][d-1]); ties keep the drift
+        auto order = [&](int h, float v) {
+            bit <<= 1;
+            const float up = __shfl_up_sync(0xffffffffu, best, 1);     // lane 0 reads its own: no increment
+            const uint32_t upp = __shfl_up_sync(0xffffffffu, pth, 1);
+            const bool inc = up > best;
+            best = (inc ? up : best) + v;
+            pth = inc ? (upp | bit) : pth;
+            const float2 tt = wtab[warp][h - 1];
+            const float snr = fmaf(best, tt.x, -tt.y);
+            if (snr > lsnr) {
+                lsnr = snr;
+                lh = h;
+                lpath = pth;
+            }
+        };
+        // with mitigation, order 32 also reaches drift 32 (lane 31's second state): that order is
+        // taken after the loop
+        const bool peel = mit && Hn == 32;
+        const int Hl = peel ? 31 : Hn;
+        const float v32 = (peel && lane == 31) ? ld_x<T, WHITEN>(x, wv, 32u * n32 + 32u) : NEG;
+        for (int h0 = 2; h0 <= Hl; h0 += PF) {
 #pragma unroll
-            for (int j = 0; j + 1 < PF; ++j) q[j] = q[j + 1];
-            {
-                const int k = h + PF, dk = dnew + PF;   // order entering the queue
-                q[PF - 1] = (k <= Hn && lane <= dk) ? ld_x<T, WHITEN>(x, wv, hn + static_cast<uint32_t>(PF) * n32 + lane)
-                                                   : NEG;
-            }
-            float up = __shfl_up_sync(0xffffffffu, best, 1);
-            if (lane == 0) up = NEG;
-            const float stay = lane <= dmax ? best : NEG;
-            const bool inc = up > stay;          // ties keep the drift
-            const float take = inc ? up : stay;
-            const float prev31 = best;
-            best = (lane <= dnew && take != NEG) ? take + v : NEG;
-            bits |= static_cast<uint32_t>(inc) << (h - 1);
-            if (lane == 31 && dnew == 32) b32 = prev31 + v32;   // only predecessor: drift 31
-            cu = ordered_bits(best);
-            if (lane == 31 && dnew == 32) {
-                const unsigned int c32 = ordered_bits(b32);
-                cu = c32 > cu ? c32 : cu;
-            }
-            m = __reduce_max_sync(0xffffffffu, cu);
-            t = wtab[warp][h - 1];
-            const float sh = __uint_as_float((m & 0x80000000u) ? (m & 0x7fffffffu) : ~m);
-            const float snr = fmaf(sh, t.x, -t.y);
-            if (snr > bsnr) {
-                bsnr = snr;
-                bh = h;
-                win = __ballot_sync(0xffffffffu, ordered_bits(best) == m);
-                // lowest drift holding the optimum; drift 32 only when it alone does
-                bd = win ? __ffs(win) - 1 : 32;
-            }
-            dmax = dnew;
-        }
-        // an optimal path of order bh: walk the recorded increments back from drift bd
-        uint32_t path = 0;
-        int d = bd;
-        for (int k = bh; k >= 2; --k) {
-            const uint32_t bk = __shfl_sync(0xffffffffu, bits, d & 31);
-            const bool step = (d == 32) || ((bk >> (k - 1)) & 1u);
-            if (step) {
-                path |= 1u << (k - 1);
-                --d;
+            for (int j = 0; j < PF; ++j) {
+                const int h = h0 + j;
+                if (h > Hl) break;
+                const float v = q[j];
+                const int k = h + PF;
+                q[j] = (k <= Hn && k >= lk) ? ld_x<T, WHITEN>(x, wv, kn + lane) : NEG;
+                kn += n32;
+                order(h, v);
             }
         }
-        if (d == 1) path |= 1u;   // order 1 chose drift 1 (mitigation)
+        if (peel) {
+            const float prev = best;             // lane 31: best sum at drift 31 after order 31
+            const uint32_t pprev = pth;
+            order(32, q[(32 - 2) % PF]);         // the loop stopped at order 32 = h0 + (32 - 2) % PF
+            t = wtab[warp][31];
+            if (lane == 31) {                    // drift 32: its only predecessor is drift 31
+                const float s32 = fmaf(prev + v32, t.x, -t.y);
+                if (s32 > lsnr) {
+                    lsnr = s32;
+                    lh = 32;
+                    ld = 32;
+                    lpath = pprev | (1u << 31);
+                }
+            }
+        }
+        // the warp's maximum: largest SNR, then lowest h, then lowest drift; its lane holds the path
+        unsigned long long key = (static_cast<unsigned long long>(ordered_bits(lsnr)) << 32) |
+                                 (static_cast<unsigned long long>(63 - lh) << 6) | static_cast<unsigned long long>(63 - ld);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+            key = k2 > key ? k2 : key;
+        }
+        const unsigned int kb = static_cast<unsigned int>(key >> 32);
+        const float bsnr = __uint_as_float((kb & 0x80000000u) ? (kb & 0x7fffffffu) : ~kb);
+        const int bh = 63 - static_cast<int>((key >> 6) & 63u);
+        const int bd = 63 - static_cast<int>(key & 63u);
+        const uint32_t path = __shfl_sync(0xffffffffu, lpath, bd & 31);
         if (lane == 0) {
             const int64_t oi = fb + n;
             o.snr[oi] = bsnr;
