@@ -57,6 +57,8 @@ KERNEL_SOURCES = {
     "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
     "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
     "plane": ["hs_fwd2d.cu"],
+    "plane16": ["hs_fwd2d.cu"],
+    "planebf16": ["hs_fwd2d.cu"],
     "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
 }
 
@@ -501,11 +503,16 @@ def wl_batch(args, hs, torch, dev, world, dist):
 
 def wl_plane(args, hs, torch, dev, world, dist):
     H = 8
+    wl = args.workload
+    dtype = {"plane": hs.F32, "plane16": hs.F16, "planebf16": hs.BF16}[wl]
+    elem = 4 if dtype == hs.F32 else 2
     tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
     pl = synth.device_plane(synth.PLANE_N_FREQ, synth.PLANE_N_ROWS, synth.PLANE_Z0_ROW, synth.SEED_BASE + 4,
                             tracks, dev)
+    if dtype != hs.F32:
+        pl = pl.to(torch.float16 if dtype == hs.F16 else torch.bfloat16)
     plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=synth.PLANE_N_FREQ, n_rows=synth.PLANE_N_ROWS,
-                   z0_row=synth.PLANE_Z0_ROW, device=dev.index)
+                   z0_row=synth.PLANE_Z0_ROW, dtype=dtype, device=dev.index)
     if args.tuning:
         plan.tuning = json.loads(args.tuning)
     nfund = plan.total_fundamentals
@@ -531,21 +538,26 @@ def wl_plane(args, hs, torch, dev, world, dist):
     peak, peak_kind = measured_peaks()
     gold = (load_json(GOLDEN) or {}).get("plane", {})
     if "sectors" in gold:
-        alg, how = int(gold["sectors"]) * 32, "oracle sector footprint"
+        # the FP32 footprint; a 16-bit plane touches the same bins in half the bytes
+        alg = int(gold["sectors"]) * 32 * elem // 4
+        how = "oracle sector footprint" + ("" if elem == 4 else " of the FP32 plane x 1/2")
     else:
-        alg, how = synth.PLANE_N_FREQ * synth.PLANE_N_ROWS * 4, "whole input"
+        alg, how = synth.PLANE_N_FREQ * synth.PLANE_N_ROWS * elem, "whole input"
     alg += nfund * (4 + 1 + 4) + 2 * 4 * H
     result = {
         "metric": METRIC, "value": world * nfund * H / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "2D greedy over an f-fdot plane 201 x 2^21 (FP32), H=8, 8 drifting signals",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {hs.F32: "f32", hs.F16: "f16 storage, f32 accumulate", hs.BF16: "bf16 storage, f32 accumulate"}[dtype],
+        "data": "synthetic",
+        "config": {"workload": "2D greedy over an f-fdot plane 201 x 2^21 (%s), H=8, 8 drifting signals"
+                               % {hs.F32: "FP32", hs.F16: "FP16", hs.BF16: "BF16"}[dtype],
                    "fundamentals": int(nfund), "H": H, "domain": list(plan.domain), "tuning": plan.tuning.as_dict(),
                    "l2": "input larger than L2 (no flush)"},
-        "roofline": roofline(alg, ms, peak, peak_kind, "plane", how, plan.tuning.as_dict()),
+        "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }
-    host_plane = pl.cpu().numpy()
+    host_plane = pl.float().cpu().numpy()
     return result, clk.summary(), lambda: oracle_rate_2d(host_plane, synth.PLANE_Z0_ROW, H, budget_s=10.0)
 
 
@@ -675,7 +687,7 @@ def wl_table2(args, hs, torch, dev, world, dist):
 
 
 WORKLOADS = {"long": wl_long, "long16": wl_long, "longbf16": wl_long, "batch": wl_batch, "batch16": wl_batch,
-             "plane": wl_plane, "grad": wl_grad, "table2": wl_table2}
+             "plane": wl_plane, "plane16": wl_plane, "planebf16": wl_plane, "grad": wl_grad, "table2": wl_table2}
 
 
 def main():

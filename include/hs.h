@@ -82,7 +82,7 @@ typedef struct {
     int32_t H;               /* harmonics summed: 1..32 (1D), 1..8 (2D) */
     int32_t forms;           /* any of HS_FORM_SIMPLE | HS_FORM_GREEDY | HS_FORM_OPTIMAL (2D:
                                 HS_FORM_GREEDY only) */
-    int32_t dtype;           /* hs_dtype of the stored input (2D: HS_F32 only) */
+    int32_t dtype;           /* hs_dtype of the stored input (spectra or plane); FP32 accumulation */
     int64_t num_spectra;     /* B >= 1 (1D); 1 for 2D */
     const int64_t *lengths;  /* host [B]: N_s bins of spectrum s, H + 1 <= N_s < 2^31 - 64 (1D) */
     const int64_t *offsets;  /* host [B] or NULL: element offset of spectrum s in the concatenated

@@ -336,7 +336,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     if (greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
     if (p->d.dims == 2) {
         Fwd2DArgs a{};
-        a.plane = static_cast<const float *>(spectra);
+        a.plane = spectra;
         a.n_freq = p->d.n_freq;
         a.n_rows = p->d.n_rows;
         a.z0_row = p->d.z0_row;
@@ -355,7 +355,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         dim3 grid = a.zfast ? dim3(static_cast<unsigned>(a.nz), static_cast<unsigned>(ftiles))
                             : dim3(static_cast<unsigned>(ftiles), static_cast<unsigned>(a.nz));
         void *args[] = {&a};
-        HS_CUDA(cudaLaunchKernel(fwd2d_kernel(), grid, dim3(threads), args, 0, st));
+        HS_CUDA(cudaLaunchKernel(fwd2d_kernel(p->d.dtype), grid, dim3(threads), args, 0, st));
         return HS_OK;
     }
     const hs_tuning &t = p->tun;
@@ -754,7 +754,6 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         p->path_bytes = d.H <= 8 ? 1 : (d.H <= 16 ? 2 : 4);
     } else if (d.dims == 2) {
         if (d.H < 1 || d.H > kMaxH2D || d.forms != HS_FORM_GREEDY) { delete p; return HS_ERR_INVALID_ARG; }
-        if (d.dtype != HS_F32) { delete p; return HS_ERR_UNSUPPORTED; }
         if (d.num_spectra != 1) { delete p; return HS_ERR_INVALID_ARG; }
         if (d.flags & (HS_FLAG_WHITENING | HS_FLAG_PER_SPECTRUM_NORM | HS_FLAG_TRUNCATE_TAIL)) { delete p; return HS_ERR_UNSUPPORTED; }
         if (d.n_freq < 3 || d.n_rows < 3 || d.z0_row < 0 || d.z0_row >= d.n_rows) { delete p; return HS_ERR_INVALID_ARG; }

@@ -3,10 +3,13 @@
 // higher-dimensional sum (acceleration search) without giving an algorithm; the rule here
 // is: best value starts at the centre, the 8 neighbours are scanned in raster order
 // (dz = -1..1 outer, df = -1..1 inner) and replace it only when strictly larger.
+// The plane is stored as FP32, FP16 or BF16; each value is widened exactly to FP32, so the
+// comparisons are those of the stored values and the sum accumulates in FP32.
 #include "hs_fwd1d.cuh"
 
 namespace hs {
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
 {
     __shared__ float rs[kMaxH2D], murs[kMaxH2D];
@@ -42,12 +45,12 @@ __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
                     break;
                 }
             }
-            const float *r0 = a.plane + (cr - 1) * nfq + cf;   // row z - 1, column cf
-            const float *r1 = r0 + nfq;
-            const float *r2 = r1 + nfq;
-            const float c00 = __ldg(r0 - 1), c01 = __ldg(r0), c02 = __ldg(r0 + 1);
-            const float c10 = __ldg(r1 - 1), c11 = __ldg(r1), c12 = __ldg(r1 + 1);
-            const float c20 = __ldg(r2 - 1), c21 = __ldg(r2), c22 = __ldg(r2 + 1);
+            const T *r0 = static_cast<const T *>(a.plane) + (cr - 1) * nfq + cf;   // row z - 1, column cf
+            const T *r1 = r0 + nfq;
+            const T *r2 = r1 + nfq;
+            const float c00 = ld_raw<T, int64_t>(r0, -1), c01 = ld_raw<T, int64_t>(r0, 0), c02 = ld_raw<T, int64_t>(r0, 1);
+            const float c10 = ld_raw<T, int64_t>(r1, -1), c11 = ld_raw<T, int64_t>(r1, 0), c12 = ld_raw<T, int64_t>(r1, 1);
+            const float c20 = ld_raw<T, int64_t>(r2, -1), c21 = ld_raw<T, int64_t>(r2, 0), c22 = ld_raw<T, int64_t>(r2, 1);
             float v = c11;
             int code = 4;
             if (c00 > v) { v = c00; code = 0; }
@@ -72,6 +75,14 @@ __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
     if (a.g.argmax) block_argmax(valid ? argmax_key(best, o) : 0ull, a.g.argmax, red);
 }
 
-const void *fwd2d_kernel() { return reinterpret_cast<const void *>(&k_fwd2d); }
+const void *fwd2d_kernel(int dtype)
+{
+    switch (dtype) {
+    case HS_F32: return reinterpret_cast<const void *>(&k_fwd2d<float>);
+    case HS_F16: return reinterpret_cast<const void *>(&k_fwd2d<__half>);
+    case HS_BF16: return reinterpret_cast<const void *>(&k_fwd2d<__nv_bfloat16>);
+    }
+    return nullptr;
+}
 
 }  // namespace hs

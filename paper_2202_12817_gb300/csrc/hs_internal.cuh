@@ -86,7 +86,7 @@ constexpr int kWinStaticSmem = 2048;  // static shared memory of the window kern
 
 // 2D forward launch arguments.
 struct Fwd2DArgs {
-    const float *plane;
+    const void *plane;             // [n_rows][n_freq] of the plan's dtype
     int64_t n_freq;
     int64_t n_rows;
     int64_t z0_row;
@@ -137,7 +137,7 @@ struct Bwd1DArgs {
 const void *fwd1d_kernel_f32(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
-const void *fwd2d_kernel();
+const void *fwd2d_kernel(int dtype);
 const void *fwd1d_opt_kernel(int dtype, int whitening);
 // 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 per CTA
 const void *fwd1d_tail_kernel_f32(int forms, int whitening);

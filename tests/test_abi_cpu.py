@@ -87,6 +87,13 @@ def test_plan_2d_domain(hs):
     assert p.total_fundamentals == 262142 * 23
 
 
+def test_plan_2d_reduced_precision(hs):
+    """2D plans take FP16 / BF16 planes with the same domain as FP32."""
+    for dt in (hs.F16, hs.BF16):
+        p = plan(hs, H=8, forms=hs.GREEDY, dims=2, n_freq=1 << 21, n_rows=201, z0_row=100, dtype=dt)
+        assert p.domain == (1, 262142, -11, 11) and p.extent == 201 << 21
+
+
 def test_plan_2d_domain_matches_oracle(hs, oracle_lib):
     for nf, nr, z0, H in [(5000, 41, 20, 3), (1000, 30, 10, 4), (777, 9, 4, 1)]:
         p = plan(hs, H=H, forms=hs.GREEDY, dims=2, n_freq=nf, n_rows=nr, z0_row=z0)
@@ -109,6 +116,7 @@ def test_plan_2d_domain_matches_oracle(hs, oracle_lib):
     dict(H=4, forms=1, dims=2, n_freq=1000, n_rows=41, z0_row=20),
     dict(H=4, forms=2, dims=2, n_freq=1000, n_rows=5, z0_row=2),   # no z fits
     dict(H=4, forms=2, dims=3, n_freq=1000, n_rows=41, z0_row=20),
+    dict(H=4, forms=2, dims=2, n_freq=1000, n_rows=41, z0_row=20, dtype=3),
 ])
 def test_plan_rejects(hs, kw):
     with pytest.raises(hs.HSError) as e:

@@ -13,16 +13,23 @@ DEV = torch.device("cuda", 0)
 # ---------------------------------------------------------------------------------------------
 # 2D greedy
 # ---------------------------------------------------------------------------------------------
-def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None):
+def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0):
+    """dtype 1 / 2: the plane is rounded to FP16 / BF16 on the host (round to nearest even) and
+    the oracle runs on the rounded values, which FP32 holds exactly."""
     n_rows, n_freq = pl.shape
-    plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=flags)
+    if dtype:
+        t = torch.from_numpy(pl).to({1: torch.float16, 2: torch.bfloat16}[dtype])
+        pl_dev, pl = t.to(DEV), t.float().numpy()
+    else:
+        pl_dev = torch.from_numpy(pl).to(DEV)
+    plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=flags, dtype=dtype)
     if order is not None:
         plan.tuning = dict(kernel=order, threads=256)     # 0: f-tiles fastest, 1: z rows fastest
         assert plan.tuning.kernel == order
     assert plan.domain == o.domain_2d(n_freq, n_rows, z0, H)
     mu, sg = hs.norm_exponential(2, 2, H, True, mean1)
     ng = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
-    out = plan.forward(torch.from_numpy(pl).to(DEV), None, ng)[hs.GREEDY]
+    out = plan.forward(pl_dev, None, ng)[hs.GREEDY]
     torch.cuda.synchronize()
     hs.check_device_error(plan)
     r_snr, r_bh, r_path, r_all = o.greedy_2d(pl, z0, H, mu, sg, want_all=True)
@@ -52,6 +59,22 @@ def test_2d_integer_ties(hs, oracle_lib):
     run_2d(hs, oracle_lib, pl, 20, 5)
 
 
+@pytest.mark.parametrize("dtype", [1, 2])
+@pytest.mark.parametrize("H", [3, 8])
+def test_2d_reduced_precision(hs, oracle_lib, H, dtype):
+    """FP16 / BF16 plane storage: comparisons on the stored values, FP32 sums."""
+    z0 = 30
+    pl = synth.plane(5003, 2 * z0 + 1, z0, 70 + H, synth.random_tracks(3, 5003, 18, f_lo=50, zmax=3))
+    for order in (0, 1):
+        run_2d(hs, oracle_lib, pl, z0, H, order=order, dtype=dtype)
+
+
+def test_2d_integer_ties_bf16(hs, oracle_lib):
+    """Small integers are exact in BF16: dense ties exercise the strict raster-order rule."""
+    pl = np.floor(synth.plane(2048, 41, 20, 9) * 0.7).astype(np.float32)
+    run_2d(hs, oracle_lib, pl, 20, 5, dtype=2, flags=hs.FLAG_CHECKED)
+
+
 def test_2d_full_size(hs, oracle_lib):
     """f-fdot plane 201 x 2^21, H = 8, chi-square(2) noise + 8 drifting tracks."""
     tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
@@ -59,6 +82,8 @@ def test_2d_full_size(hs, oracle_lib):
     for order in (0, 1):
         near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, order=order)
         assert near <= 20
+    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, dtype=1)
+    assert near <= 20
 
 
 # ---------------------------------------------------------------------------------------------
