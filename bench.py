@@ -405,14 +405,22 @@ def wl_long(args, hs, torch, dev, world, dist):
     wt = time_steps(torch, step, min(args.steps, 300), stream)
     w_ms = sum(wt) / len(wt)
 
-    # end to end through the C ABI with host buffers: pinned H2D of the spectrum, run,
-    # D2H of every output, all inside the timed region
+    # end to end through the C ABI with host buffers: hs_run_host copies the pinned spectrum in
+    # chunks and runs each chunk's fundamentals once their bins have arrived, and copies every
+    # output back to pinned host memory, all inside the timed region
     xh = x.cpu().pin_memory()
-    dev_outs = (s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax)
-    outs_h = [torch.empty_like(t, device="cpu").pin_memory() for t in dev_outs]
+    host_s, host_g = plan.alloc_form_host(path=False), plan.alloc_form_host()
+    outs_h = [t for t in (host_s.snr, host_s.best_h, host_s.argmax, host_g.snr, host_g.best_h, host_g.path,
+                          host_g.argmax)]
     xd2 = torch.empty_like(x)
 
     def e2e_step():
+        hs.run_host(plan, xh, xd2, None, s_io, g_io, host_s, host_g, ws, stream)
+
+    # the same with one copy before the pass and the outputs copied after it (context)
+    dev_outs = (s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax)
+
+    def serial_step():
         xd2.copy_(xh, non_blocking=True)
         hs.run(plan, xd2, None, s_io, g_io, ws, stream)
         for hbuf, dbuf in zip(outs_h, dev_outs):
@@ -420,8 +428,11 @@ def wl_long(args, hs, torch, dev, world, dist):
 
     for _ in range(2):
         e2e_step()
+        serial_step()
     et = time_steps(torch, e2e_step, max(3, min(args.steps, 30)), stream)
     e_ms = max_over_ranks(sum(et) / len(et), dist, dev)
+    st_ = time_steps(torch, serial_step, max(3, min(args.steps, 30)), stream)
+    s_ms = sum(st_) / len(st_)
 
     result = {
         "metric": METRIC, "value": world * units / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
@@ -442,7 +453,9 @@ def wl_long(args, hs, torch, dev, world, dist):
                     "note": "input left in L2 between steps (no flush): context, not the headline"},
         "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(x.numel() * x.element_size()),
-                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in outs_h))},
+                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in outs_h)),
+                "ms": round(e_ms, 5), "api": "hs_run_host (chunked copies overlapped with the pass)",
+                "copy_then_run": {"value": world * units / (s_ms / 1e3), "ms": round(s_ms, 5)}},
         "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 3),
     }
     xs_host = x.float().cpu().numpy()

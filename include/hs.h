@@ -174,6 +174,28 @@ hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_form_io *simple,
                  const hs_form_io *greedy, void *workspace, void *stream);
 
+/* Forward pass from host memory, the same results as hs_run.  host_spectra: the input in the
+ * plan's layout (hs_plan_input_offsets, extent elements), in page-locked host memory; spectra:
+ * a device buffer of extent elements that receives it (16-byte aligned, distinct from
+ * host_spectra).  The input is copied in chunks on a stream owned by the plan, and each chunk's
+ * fundamentals run on `stream` as soon as the bins they read have arrived (fundamental n reads
+ * up to bin H n + H): one spectrum is cut into ranges of fundamentals, a batch into groups of
+ * whole spectra (hs_plan_set_host_chunks; one chunk when the spectra do not lie in increasing
+ * order, and for 2D plans).  simple / greedy: device outputs as for hs_run.
+ * host_simple / host_greedy: NULL, or page-locked host copies of the same outputs (mu and sigma
+ * unused; a NULL field is not copied); each chunk's outputs are copied back on a second plan
+ * stream while later chunks run (after the whole pass with HS_FLAG_TRUNCATE_TAIL, whose tail
+ * needs the whole input), the argmax after the last chunk.  Ordered on `stream`: the copies
+ * wait for work already enqueued there, and work enqueued after the call sees the outputs and
+ * the host copies.  The first call creates the plan's two copy streams and their events; after
+ * that no allocation and no synchronisation.  Calls on one plan must not overlap on the host. */
+hs_status hs_run_host(hs_plan plan, const void *host_spectra, void *spectra, const float *w,
+                      const hs_form_io *simple, const hs_form_io *greedy, const hs_form_io *host_simple,
+                      const hs_form_io *host_greedy, void *workspace, void *stream);
+/* Chunks of hs_run_host's pipeline: 1..16, or 0 for the default (about 8 MiB of input per chunk,
+ * at most 8).  A batch is cut between spectra, so it may get fewer chunks than asked for. */
+hs_status hs_plan_set_host_chunks(hs_plan plan, int32_t chunks);
+
 /* Forward pass of the optimal form (plan with HS_FORM_OPTIMAL, 1D): for every fundamental,
  * the SNR of S*_h (Eq. 2 with the caller's mu/sigma of the optimum), its maximum over h (first
  * strictly larger wins, as for the other forms), the best h and, if optimal->path is set, an

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_fixed_scratch", "run_optimal", "backward",
+__all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_host", "run_fixed_scratch", "run_optimal", "backward",
            "norm_exponential", "OPTIMAL",
            "check_device_error", "decode_argmax", "status_string", "SIMPLE", "GREEDY", "F32", "F16", "BF16",
            "FLAG_NO_MITIGATION", "FLAG_PER_SPECTRUM_NORM", "FLAG_WHITENING", "FLAG_AUTOTUNE", "FLAG_GRAPH",
@@ -98,6 +98,9 @@ def lib():
         L.hs_run.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V, _V]
         L.hs_backward.argtypes = [_V, _I32, _V, ctypes.POINTER(_FormIO), _V, _V, _V, _V, _V, _V]
         L.hs_run_fixed_scratch.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V]
+        L.hs_plan_set_host_chunks.argtypes = [_V, _I32]
+        L.hs_run_host.argtypes = [_V, _V, _V, _V, ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO),
+                                  ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V, _V]
         L.hs_run_optimal.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), _V]
         L.hs_check_device_error.argtypes = [_V, _V]
         L.hs_norm_exponential.argtypes = [_I32, _I32, _I32, _I32, ctypes.c_double, _V, _V]
@@ -295,6 +298,25 @@ class Plan:
                       torch.empty(F, dtype=self.path_dtype(), device=dev) if path else None,
                       torch.empty(self.B, dtype=torch.int64, device=dev) if argmax else None)
 
+    @property
+    def host_chunks(self) -> int:
+        return getattr(self, "_host_chunks", 0)
+
+    @host_chunks.setter
+    def host_chunks(self, k: int):
+        """Chunks of ``run_host``'s pipeline (0: about 8 MiB of input per chunk)."""
+        _check(lib().hs_plan_set_host_chunks(self._h, int(k)), "hs_plan_set_host_chunks")
+        self._host_chunks = int(k)
+
+    def alloc_form_host(self, path=True, argmax=True):
+        """Pinned host buffers for the outputs of one form (for ``run_host``): snr, best_h, path, argmax."""
+        import torch
+        F = self.total_fundamentals
+        return FormIO(None, None, torch.empty(F, dtype=torch.float32).pin_memory(),
+                      torch.empty(F, dtype=torch.uint8).pin_memory(),
+                      torch.empty(F, dtype=self.path_dtype()).pin_memory() if path else None,
+                      torch.empty(self.B, dtype=torch.int64).pin_memory() if argmax else None)
+
     def forward(self, spectra, simple_norm=None, greedy_norm=None, w=None, path=True, argmax=True, stream=None,
                 optimal_norm=None):
         """Run the planned forms; ``*_norm`` = (mu, sigma) device tensors.  Returns {form: FormIO}."""
@@ -321,6 +343,23 @@ def run(plan: Plan, spectra, w=None, simple: FormIO | None = None, greedy: FormI
     cg = greedy._c() if greedy is not None else None
     _check(lib().hs_run(plan.handle, _ptr(spectra), _ptr(w), ctypes.byref(cs) if cs else None,
                         ctypes.byref(cg) if cg else None, _ptr(ws), _stream_ptr(stream)), "hs_run")
+
+
+def run_host(plan: Plan, host_spectra, spectra, w=None, simple: FormIO | None = None, greedy: FormIO | None = None,
+             host_simple: FormIO | None = None, host_greedy: FormIO | None = None, workspace=None, stream=None):
+    """hs_run_host: copy ``host_spectra`` (pinned CPU tensor in the plan's layout) into the device
+    tensor ``spectra`` chunk by chunk while the chunks already copied run; optional pinned host
+    copies of the outputs (``plan.alloc_form_host``) come back chunk by chunk.  Ordered on
+    ``stream`` (default: torch's current stream)."""
+    ws = workspace if workspace is not None else plan.workspace(spectra.device)
+    cs = simple._c() if simple is not None else None
+    cg = greedy._c() if greedy is not None else None
+    hs_ = host_simple._c() if host_simple is not None else None
+    hg = host_greedy._c() if host_greedy is not None else None
+    _check(lib().hs_run_host(plan.handle, _ptr(host_spectra), _ptr(spectra), _ptr(w),
+                             ctypes.byref(cs) if cs else None, ctypes.byref(cg) if cg else None,
+                             ctypes.byref(hs_) if hs_ else None, ctypes.byref(hg) if hg else None,
+                             _ptr(ws), _stream_ptr(stream)), "hs_run_host")
 
 
 def run_fixed_scratch(plan: Plan, spectra, w=None, simple: FormIO | None = None, greedy: FormIO | None = None,

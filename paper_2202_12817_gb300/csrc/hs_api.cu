@@ -36,6 +36,7 @@ constexpr uint32_t kKnownFlags = HS_FLAG_NO_MITIGATION | HS_FLAG_PER_SPECTRUM_NO
                                  HS_FLAG_AUTOTUNE | HS_FLAG_GRAPH | HS_FLAG_NO_DEVICE | HS_FLAG_CHECKED |
                                  HS_FLAG_TRUNCATE_TAIL;
 constexpr size_t kWorkspaceBytes = 256;     // tile counter of the dynamic schedule
+constexpr int kMaxChunks = 16;               // chunks of the pipelined host input
 constexpr int kBwdBlockBins = 1024;   // must stay <= 32767 (int16 offsets)
 constexpr int kBwdMaxGroups = 16;     // spectrum groups of the adjoint's dL/dw partial sums
 constexpr int kBwdThreads = 256;
@@ -92,6 +93,20 @@ struct hs_plan_s {
     GraphKey gkey{};
     bool gvalid = false;
     std::mutex mu;
+    // pipelined host input (hs_run_host): chunks of tiles with the input range their bins lie in
+    // and the output range they write; each chunk launches on a tile prefix shifted to its
+    // first tile (d_chunk_tile_start, kMaxChunks x (B+1))
+    struct Chunk {
+        int64_t t_a, t_b;        // tiles [t_a, t_b) of the main pass
+        int64_t in_lo, in_hi;    // input elements [in_lo, in_hi) copied before the chunk runs
+        int64_t out_lo, out_hi;  // outputs [out_lo, out_hi) the chunk completes
+    };
+    std::vector<Chunk> chunks;
+    bool chunk_out = false;      // outputs can be copied back chunk by chunk (no truncated tail)
+    int host_chunks = 0;         // requested chunk count (0: about 8 MiB of input per chunk)
+    int64_t *d_chunk_tile_start = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kMaxChunks] = {}, ev_out[kMaxChunks] = {};
 };
 
 namespace {
@@ -143,6 +158,62 @@ size_t bwd_workspace_bytes(const hs_plan p)
 }
 void make_win_plan(hs_plan p);
 
+// Chunks of the pipelined host input (1D).  Fundamental n reads bins up to H n + H, so the
+// tiles ending at fundamental n_b need the input only up to H n_b + 1 (plus a margin for the
+// 16-byte-rounded window copies); one spectrum is cut into tile ranges, a batch into groups of
+// whole spectra.  By default about 8 MiB of input per chunk, at most 8 (hs_plan_set_host_chunks
+// sets the count, up to kMaxChunks); a batch whose spectra do not lie in increasing order is one
+// chunk.
+void make_chunks(hs_plan p)
+{
+    p->chunks.clear();
+    p->chunk_out = !(p->d.flags & HS_FLAG_TRUNCATE_TAIL);
+    if (p->d.dims != 1) return;
+    const int64_t B = static_cast<int64_t>(p->nf.size());
+    const int64_t T = tile_fund(p->d, p->tun);
+    const int64_t H = p->d.H;
+    const int64_t eb = elem_bytes(p->d.dtype);
+    bool ordered = true;
+    for (int64_t s = 0; s + 1 < B; ++s)
+        if (p->in_off[s] + p->len[s] > p->in_off[s + 1]) ordered = false;
+    const int64_t want = p->host_chunks > 0 ? p->host_chunks
+                                            : std::max<int64_t>(1, std::min<int64_t>(8, p->extent * eb / (8ll << 20)));
+    const int64_t K = ordered ? want : 1;
+    const int64_t total = p->tile_start[B];
+    if (K == 1 || total == 0) {
+        p->chunks.push_back({0, total, 0, p->extent, 0, p->total_fund});
+        return;
+    }
+    if (B == 1) {
+        const int64_t base = p->in_off[0], len = p->len[0], nf = p->nf_main[0];
+        int64_t lo = base;
+        for (int64_t c = 0; c < K; ++c) {
+            const int64_t t_a = total * c / K, t_b = total * (c + 1) / K;
+            if (t_b <= t_a) continue;
+            const int64_t n_b = std::min(nf, t_b * T);
+            int64_t need = c + 1 == K ? len : std::min(len, H * n_b + 1 + 32);
+            int64_t hi = base + need;
+            if (c + 1 < K) hi = std::min(p->extent, (hi + 15) / 16 * 16);
+            else hi = p->extent;
+            p->chunks.push_back({t_a, t_b, lo, std::max(lo, hi), p->fund_off[0] + t_a * T, p->fund_off[0] + n_b});
+            lo = std::max(lo, hi);
+        }
+        return;
+    }
+    // whole spectra per chunk, about extent / K elements each
+    int64_t s0 = 0;
+    for (int64_t c = 0; c < K && s0 < B; ++c) {
+        int64_t s1 = s0 + 1;
+        const int64_t goal = p->extent * (c + 1) / K;
+        while (s1 < B && (c + 1 == K || p->in_off[s1] + p->len[s1] <= goal)) ++s1;
+        if (c + 1 == K) s1 = B;
+        const int64_t lo = s0 == 0 ? 0 : p->in_off[s0];
+        const int64_t hi = s1 == B ? p->extent : p->in_off[s1];
+        p->chunks.push_back({p->tile_start[s0], p->tile_start[s1], lo, hi, p->fund_off[s0], p->fund_off[s1]});
+        s0 = s1;
+    }
+}
+
 void compute_tiles(hs_plan p)
 {
     const int64_t T = tile_fund(p->d, p->tun);
@@ -154,6 +225,7 @@ void compute_tiles(hs_plan p)
     for (size_t s = 0; s < B; ++s)
         p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailThreads - 1) / kTailThreads;
     make_win_plan(p);
+    make_chunks(p);
 }
 
 hs_status upload_tiles(hs_plan p)
@@ -161,6 +233,14 @@ hs_status upload_tiles(hs_plan p)
     if (p->no_device || p->d.dims != 1) return HS_OK;
     HS_CUDA(cudaMemcpy(p->d_tile_start, p->tile_start.data(), sizeof(int64_t) * p->tile_start.size(),
                        cudaMemcpyHostToDevice));
+    if (p->d_chunk_tile_start) {
+        const size_t B1 = p->tile_start.size();
+        std::vector<int64_t> shifted(p->chunks.size() * B1);
+        for (size_t c = 0; c < p->chunks.size(); ++c)
+            for (size_t s = 0; s < B1; ++s) shifted[c * B1 + s] = p->tile_start[s] - p->chunks[c].t_a;
+        HS_CUDA(cudaMemcpy(p->d_chunk_tile_start, shifted.data(), sizeof(int64_t) * shifted.size(),
+                           cudaMemcpyHostToDevice));
+    }
     return HS_OK;
 }
 
@@ -273,6 +353,15 @@ void free_plan(hs_plan p)
         cudaFree(p->d_tail_tile_start);
         cudaFree(p->d_in_len);
         cudaFree(p->d_err);
+        cudaFree(p->d_chunk_tile_start);
+        if (p->h2d) cudaStreamDestroy(p->h2d);
+        if (p->d2h) cudaStreamDestroy(p->d2h);
+        if (p->ev_start) cudaEventDestroy(p->ev_start);
+        if (p->ev_done) cudaEventDestroy(p->ev_done);
+        for (int i = 0; i < kMaxChunks; ++i) {
+            if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+            if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+        }
     }
     delete p;
 }
@@ -328,12 +417,15 @@ hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t 
 }
 
 // Enqueue the forward pass (memsets + the main kernel + the truncated tail's) on `st`.
+// chunk >= 0 (1D): only the tiles of that chunk of the pipelined host input, on the tile prefix
+// shifted to its first tile, without the argmax reset (done once before the first chunk), the L2
+// prefetches (their input may not have arrived yet) or, but for the last chunk, the tail.
 hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
-                      const hs_form_io *greedy, void *ws, cudaStream_t st)
+                      const hs_form_io *greedy, void *ws, cudaStream_t st, int chunk = -1)
 {
     const int64_t B = p->d.dims == 1 ? p->d.num_spectra : 1;
-    if (simple && simple->argmax) HS_CUDA(cudaMemsetAsync(simple->argmax, 0, sizeof(uint64_t) * B, st));
-    if (greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
+    if (chunk < 0 && simple && simple->argmax) HS_CUDA(cudaMemsetAsync(simple->argmax, 0, sizeof(uint64_t) * B, st));
+    if (chunk < 0 && greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
     if (p->d.dims == 2) {
         Fwd2DArgs a{};
         a.plane = spectra;
@@ -383,6 +475,13 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.s = to_form_args(simple);
     a.g = to_form_args(greedy);
     a.err = p->d_err;
+    const bool last = chunk < 0 || chunk + 1 == static_cast<int>(p->chunks.size());
+    if (chunk >= 0) {
+        const auto &c = p->chunks[chunk];
+        a.tile_start = p->d_chunk_tile_start + static_cast<int64_t>(chunk) * (B + 1);
+        a.total_tiles = c.t_b - c.t_a;
+        a.pf_next = 0;
+    }
     if ((p->d.forms & 3) == 0) return HS_OK;   // the optimal form runs through hs_run_optimal
     const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
     if (!fn) return HS_ERR_UNSUPPORTED;
@@ -397,18 +496,18 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
             if (per_sm < 1) return HS_ERR_UNSUPPORTED;
         }
         int64_t grid = std::min<int64_t>(a.total_tiles, static_cast<int64_t>(per_sm) * p->sms);
-        if (grid < 1) return HS_OK;
+        if (grid < 1) return last ? launch_tail(p, a, st) : HS_OK;
         WinPlan wp = p->wplan;
         const int64_t in_bytes = p->extent * elem_bytes(p->d.dtype);
-        if ((t.prefetch & 1) && p->l2_bytes > 0 && in_bytes <= p->l2_bytes / 4)
+        if (chunk < 0 && (t.prefetch & 1) && p->l2_bytes > 0 && in_bytes <= p->l2_bytes / 4)
             wp.pf_chunk = ((in_bytes + grid - 1) / grid + 15) / 16 * 16;
         void *args[] = {&a, &wp};
         HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(block), args, smem, st));
-        return launch_tail(p, a, st);
+        return last ? launch_tail(p, a, st) : HS_OK;
     }
     int64_t grid = a.total_tiles;
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
-    if ((t.kernel == 6 || t.kernel == 7) && (t.prefetch & 1) && p->l2_bytes > 0 && grid > 0) {
+    if (chunk < 0 && (t.kernel == 6 || t.kernel == 7) && (t.prefetch & 1) && p->l2_bytes > 0 && grid > 0) {
         // an input that fits in half of L2 is prefetched there by the first CTAs, one share each
         const int64_t in_bytes = p->extent * elem_bytes(p->d.dtype);
         if (in_bytes <= p->l2_bytes / 2) {
@@ -422,11 +521,12 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         // every CTA draws all of its tiles from this counter, starting at 0
         HS_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), st));
     }
-    if (grid < 1) return HS_OK;
     if (grid > 0x7fffffff) return HS_ERR_UNSUPPORTED;
-    void *args[] = {&a};
-    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
-    return launch_tail(p, a, st);
+    if (grid >= 1) {
+        void *args[] = {&a};
+        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
+    }
+    return last ? launch_tail(p, a, st) : HS_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -629,6 +729,64 @@ done:
     return result;
 }
 
+// Argument checks shared by hs_run and hs_run_host (device pointers).
+hs_status check_run_args(const hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
+                         const hs_form_io *greedy, const void *workspace)
+{
+    if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
+    if (w && !aligned(w, 16)) return HS_ERR_INVALID_ARG;
+    const bool want_s = (p->d.forms & HS_FORM_SIMPLE) != 0, want_g = (p->d.forms & HS_FORM_GREEDY) != 0;
+    if (want_s != (simple != nullptr) || want_g != (greedy != nullptr)) return HS_ERR_INVALID_ARG;
+    if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
+    if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
+    if (p->d.dims == 1 && p->tun.dynamic && (!workspace || !aligned(workspace, 8))) return HS_ERR_INVALID_ARG;
+    return HS_OK;
+}
+
+// Host copies of one form's outputs [lo, hi) (and its argmax when `argmax`) on `st`; fields that
+// either side leaves NULL are skipped.
+hs_status copy_outputs(const hs_plan p, const hs_form_io *dev, const hs_form_io *host, int64_t lo, int64_t hi,
+                       bool argmax, cudaStream_t st)
+{
+    if (!dev || !host || hi <= lo) return HS_OK;
+    const size_t n = static_cast<size_t>(hi - lo);
+    if (dev->snr && host->snr) HS_CUDA(cudaMemcpyAsync(host->snr + lo, dev->snr + lo, 4 * n, cudaMemcpyDeviceToHost, st));
+    if (dev->best_h && host->best_h)
+        HS_CUDA(cudaMemcpyAsync(host->best_h + lo, dev->best_h + lo, n, cudaMemcpyDeviceToHost, st));
+    if (dev->path && host->path) {
+        const size_t pb = static_cast<size_t>(p->path_bytes);
+        HS_CUDA(cudaMemcpyAsync(static_cast<unsigned char *>(host->path) + pb * lo,
+                                static_cast<const unsigned char *>(dev->path) + pb * lo, pb * n,
+                                cudaMemcpyDeviceToHost, st));
+    }
+    if (argmax && dev->argmax && host->argmax) {
+        const int64_t B = p->d.dims == 1 ? p->d.num_spectra : 1;
+        HS_CUDA(cudaMemcpyAsync(host->argmax, dev->argmax, sizeof(uint64_t) * B, cudaMemcpyDeviceToHost, st));
+    }
+    return HS_OK;
+}
+
+hs_status ensure_host_streams(hs_plan p)
+{
+    if (p->h2d) return HS_OK;
+    cudaStream_t a = nullptr, b = nullptr;
+    HS_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    if (!cuda_ok(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking))) {
+        cudaStreamDestroy(a);
+        return HS_ERR_CUDA;
+    }
+    bool ok = cuda_ok(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming)) &&
+              cuda_ok(cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming));
+    for (int i = 0; ok && i < kMaxChunks; ++i)
+        ok = cuda_ok(cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming)) &&
+             cuda_ok(cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming));
+    p->h2d = a;
+    p->d2h = b;
+    return ok ? HS_OK : HS_ERR_CUDA;
+}
+
 }  // namespace
 
 // =========================================================================================
@@ -812,7 +970,8 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         !cuda_ok(cudaMalloc(&p->d_tail_tile_start, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_nf_main, sizeof(int64_t) * (B1 - 1))) ||
         !cuda_ok(cudaMalloc(&p->d_in_len, sizeof(int64_t) * (B1 - 1))) ||
-        !cuda_ok(cudaMalloc(&p->d_err, sizeof(int)))) {
+        !cuda_ok(cudaMalloc(&p->d_err, sizeof(int))) ||
+        (d.dims == 1 && !cuda_ok(cudaMalloc(&p->d_chunk_tile_start, sizeof(int64_t) * B1 * kMaxChunks)))) {
         free_plan(p);
         return HS_ERR_OOM;
     }
@@ -875,6 +1034,17 @@ hs_status hs_plan_workspace(hs_plan p, size_t *bytes)
     return HS_OK;
 }
 
+hs_status hs_plan_set_host_chunks(hs_plan p, int32_t chunks)
+{
+    if (!p || chunks < 0 || chunks > kMaxChunks) return HS_ERR_INVALID_ARG;
+    p->host_chunks = chunks;
+    if (p->d.dims != 1) return HS_OK;
+    make_chunks(p);
+    DeviceGuard guard(p->device);
+    if (!p->no_device && !guard.ok) return HS_ERR_CUDA;
+    return upload_tiles(p);
+}
+
 hs_status hs_plan_get_tuning(hs_plan p, hs_tuning *t)
 {
     if (!p || !t) return HS_ERR_INVALID_ARG;
@@ -913,15 +1083,8 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
 {
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
-    if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
-    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
-    if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
-    if (w && !aligned(w, 16)) return HS_ERR_INVALID_ARG;
-    const bool want_s = (p->d.forms & HS_FORM_SIMPLE) != 0, want_g = (p->d.forms & HS_FORM_GREEDY) != 0;
-    if (want_s != (simple != nullptr) || want_g != (greedy != nullptr)) return HS_ERR_INVALID_ARG;
-    if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
-    if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
-    if (p->d.dims == 1 && p->tun.dynamic && (!workspace || !aligned(workspace, 8))) return HS_ERR_INVALID_ARG;
+    const hs_status vs = check_run_args(p, spectra, w, simple, greedy, workspace);
+    if (vs != HS_OK) return vs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
@@ -969,6 +1132,76 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
         p->gvalid = true;
     }
     HS_CUDA(cudaGraphLaunch(p->gexec, st));
+    return HS_OK;
+}
+
+hs_status hs_run_host(hs_plan p, const void *host_spectra, void *spectra, const float *w, const hs_form_io *simple,
+                      const hs_form_io *greedy, const hs_form_io *host_simple, const hs_form_io *host_greedy,
+                      void *workspace, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    if (!host_spectra || host_spectra == spectra) return HS_ERR_INVALID_ARG;
+    const hs_status vs = check_run_args(p, spectra, w, simple, greedy, workspace);
+    if (vs != HS_OK) return vs;
+    if ((host_simple && !simple) || (host_greedy && !greedy)) return HS_ERR_INVALID_ARG;
+    if (host_simple && host_simple->path) return HS_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(p->mu);   // the plan's copy streams and events
+    hs_status es = ensure_host_streams(p);
+    if (es != HS_OK) return es;
+    const int64_t eb = elem_bytes(p->d.dtype);
+    const unsigned char *hsrc = static_cast<const unsigned char *>(host_spectra);
+    unsigned char *ddst = static_cast<unsigned char *>(spectra);
+    // the copies wait for the work already on `stream` (it may still read the device buffer)
+    HS_CUDA(cudaEventRecord(p->ev_start, st));
+    HS_CUDA(cudaStreamWaitEvent(p->h2d, p->ev_start, 0));
+    HS_CUDA(cudaStreamWaitEvent(p->d2h, p->ev_start, 0));
+    const bool host_out = host_simple || host_greedy;
+    const int K = p->d.dims == 1 ? static_cast<int>(p->chunks.size()) : 1;
+    if (K <= 1) {
+        HS_CUDA(cudaMemcpyAsync(ddst, hsrc, static_cast<size_t>(p->extent * eb), cudaMemcpyHostToDevice, p->h2d));
+        HS_CUDA(cudaEventRecord(p->ev_in[0], p->h2d));
+        HS_CUDA(cudaStreamWaitEvent(st, p->ev_in[0], 0));
+        es = enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+        if (es != HS_OK) return es;
+        if (host_out) {
+            HS_CUDA(cudaEventRecord(p->ev_out[0], st));
+            HS_CUDA(cudaStreamWaitEvent(p->d2h, p->ev_out[0], 0));
+            es = copy_outputs(p, simple, host_simple, 0, p->total_fund, true, p->d2h);
+            if (es == HS_OK) es = copy_outputs(p, greedy, host_greedy, 0, p->total_fund, true, p->d2h);
+            if (es != HS_OK) return es;
+        }
+    } else {
+        const int64_t B = p->d.num_spectra;
+        if (simple && simple->argmax) HS_CUDA(cudaMemsetAsync(simple->argmax, 0, sizeof(uint64_t) * B, st));
+        if (greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
+        for (int c = 0; c < K; ++c) {
+            const auto &ch = p->chunks[c];
+            if (ch.in_hi > ch.in_lo)
+                HS_CUDA(cudaMemcpyAsync(ddst + ch.in_lo * eb, hsrc + ch.in_lo * eb,
+                                        static_cast<size_t>((ch.in_hi - ch.in_lo) * eb), cudaMemcpyHostToDevice,
+                                        p->h2d));
+            HS_CUDA(cudaEventRecord(p->ev_in[c], p->h2d));
+            HS_CUDA(cudaStreamWaitEvent(st, p->ev_in[c], 0));
+            es = enqueue_fwd(p, spectra, w, simple, greedy, workspace, st, c);
+            if (es != HS_OK) return es;
+            const bool lastc = c + 1 == K;
+            if (host_out && (p->chunk_out || lastc)) {
+                HS_CUDA(cudaEventRecord(p->ev_out[c], st));
+                HS_CUDA(cudaStreamWaitEvent(p->d2h, p->ev_out[c], 0));
+                const int64_t lo = p->chunk_out ? ch.out_lo : 0, hi = p->chunk_out ? ch.out_hi : p->total_fund;
+                es = copy_outputs(p, simple, host_simple, lo, hi, lastc, p->d2h);
+                if (es == HS_OK) es = copy_outputs(p, greedy, host_greedy, lo, hi, lastc, p->d2h);
+                if (es != HS_OK) return es;
+            }
+        }
+    }
+    // `stream` continues once the last copy in either direction has been issued before it
+    HS_CUDA(cudaEventRecord(p->ev_done, p->d2h));
+    HS_CUDA(cudaStreamWaitEvent(st, p->ev_done, 0));
     return HS_OK;
 }
 

@@ -87,6 +87,16 @@ def test_plan_2d_domain(hs):
     assert p.total_fundamentals == 262142 * 23
 
 
+def test_host_chunks_setting(hs):
+    p = plan(hs, H=32, forms=3, lengths=[1 << 23])
+    for k in (0, 1, 4, 16):
+        p.host_chunks = k
+        assert p.host_chunks == k
+    for bad in (-1, 17):
+        with pytest.raises(hs.HSError):
+            p.host_chunks = bad
+
+
 def test_plan_2d_reduced_precision(hs):
     """2D plans take FP16 / BF16 planes with the same domain as FP32."""
     for dt in (hs.F16, hs.BF16):
