@@ -1241,7 +1241,7 @@ hs_status hs_run_optimal(hs_plan p, const void *spectra, const float *w, const h
     // one warp per fundamental; each warp takes a contiguous run of fundamentals
     const int threads = 256, wpc = threads / 32;
     int64_t F = p->total_fund;
-    const void *fn = fwd1d_opt_kernel(p->d.dtype, whiten ? 1 : 0);
+    const void *fn = fwd1d_opt_kernel(p->d.dtype, whiten ? 1 : 0, p->d.H, (p->d.flags & HS_FLAG_TRUNCATE_TAIL) ? 1 : 0);
     if (!fn) return HS_ERR_UNSUPPORTED;
     int occ = 0;
     HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0));

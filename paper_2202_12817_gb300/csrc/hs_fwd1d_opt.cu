@@ -18,12 +18,15 @@
 
 namespace hs {
 
-template <typename T, bool WHITEN>
-__global__ void __launch_bounds__(256, 4) k_fwd1d_opt(const Fwd1DArgs a, const FormArgs o, int64_t F, int64_t chunk)
+// HC > 0: H = HC known at compile time and no truncated-tail fundamentals, so the orders are
+// unrolled completely (no loop or bounds tests between orders); HC = 0: any H, tail included.
+// H = 8 and 32 fit in 48 registers, so five CTAs share an SM; the others keep four.
+template <typename T, bool WHITEN, int HC>
+__global__ void __launch_bounds__(256, (HC == 8 || HC == 32) ? 5 : 4) k_fwd1d_opt(const Fwd1DArgs a, const FormArgs o, int64_t F, int64_t chunk)
 {
     __shared__ int tab_spec[8];           // spectrum whose table each warp last loaded
     __shared__ float2 wtab[8][kMaxH1D];   // per warp: (1/sigma, mu/sigma) of that spectrum
-    const int H = a.H;
+    const int H = HC > 0 ? HC : a.H;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool mit = a.mitigation != 0;
     const float NEG = -INFINITY;
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd1d_opt(const Fwd1DArgs a, const F
         const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
         // orders of this fundamental: all H, or in the truncated tail those with h n + h <= N - 1
         int Hn = H;
-        if (n >= __ldg(a.nf_main + s)) {
+        if (HC == 0 && n >= __ldg(a.nf_main + s)) {
             const int64_t lim = (__ldg(a.in_len + s) - 1) / (n + 1);
             Hn = static_cast<int>(lim < H ? lim : H);
         }
@@ -121,16 +124,28 @@ __global__ void __launch_bounds__(256, 4) k_fwd1d_opt(const Fwd1DArgs a, const F
         const bool peel = mit && Hn == 32;
         const int Hl = peel ? 31 : Hn;
         const float v32 = (peel && lane == 31) ? ld_x<T, WHITEN>(x, wv, 32u * n32 + 32u) : NEG;
-        for (int h0 = 2; h0 <= Hl; h0 += PF) {
+        if constexpr (HC > 0) {
 #pragma unroll
-            for (int j = 0; j < PF; ++j) {
-                const int h = h0 + j;
-                if (h > Hl) break;
+            for (int h = 2; h <= HC; ++h) {
+                if (HC == 32 && h == 32 && peel) break;
+                const int j = (h - 2) % PF;
                 const float v = q[j];
-                const int k = h + PF;
-                q[j] = (k <= Hn && k >= lk) ? ld_x<T, WHITEN>(x, wv, kn + lane) : NEG;
+                if (h + PF <= HC) q[j] = h + PF >= lk ? ld_x<T, WHITEN>(x, wv, kn + lane) : NEG;
                 kn += n32;
                 order(h, v);
+            }
+        } else {
+            for (int h0 = 2; h0 <= Hl; h0 += PF) {
+#pragma unroll
+                for (int j = 0; j < PF; ++j) {
+                    const int h = h0 + j;
+                    if (h > Hl) break;
+                    const float v = q[j];
+                    const int k = h + PF;
+                    q[j] = (k <= Hn && k >= lk) ? ld_x<T, WHITEN>(x, wv, kn + lane) : NEG;
+                    kn += n32;
+                    order(h, v);
+                }
             }
         }
         if (peel) {
@@ -173,14 +188,21 @@ __global__ void __launch_bounds__(256, 4) k_fwd1d_opt(const Fwd1DArgs a, const F
     if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) atomicMax(o.argmax + s, kmax);
 }
 
-const void *fwd1d_opt_kernel(int dtype, int whitening)
+template <typename T, bool WHITEN>
+static const void *opt_kernel_h(int H, int tail)
 {
-    if (dtype == HS_F32) return whitening ? reinterpret_cast<const void *>(&k_fwd1d_opt<float, true>)
-                                          : reinterpret_cast<const void *>(&k_fwd1d_opt<float, false>);
-    if (dtype == HS_F16) return whitening ? reinterpret_cast<const void *>(&k_fwd1d_opt<__half, true>)
-                                          : reinterpret_cast<const void *>(&k_fwd1d_opt<__half, false>);
-    if (dtype == HS_BF16) return whitening ? reinterpret_cast<const void *>(&k_fwd1d_opt<__nv_bfloat16, true>)
-                                           : reinterpret_cast<const void *>(&k_fwd1d_opt<__nv_bfloat16, false>);
+    if (!tail && H == 32) return reinterpret_cast<const void *>(&k_fwd1d_opt<T, WHITEN, 32>);
+    if (!tail && H == 16) return reinterpret_cast<const void *>(&k_fwd1d_opt<T, WHITEN, 16>);
+    if (!tail && H == 8) return reinterpret_cast<const void *>(&k_fwd1d_opt<T, WHITEN, 8>);
+    return reinterpret_cast<const void *>(&k_fwd1d_opt<T, WHITEN, 0>);
+}
+
+const void *fwd1d_opt_kernel(int dtype, int whitening, int H, int tail)
+{
+    if (dtype == HS_F32) return whitening ? opt_kernel_h<float, true>(H, tail) : opt_kernel_h<float, false>(H, tail);
+    if (dtype == HS_F16) return whitening ? opt_kernel_h<__half, true>(H, tail) : opt_kernel_h<__half, false>(H, tail);
+    if (dtype == HS_BF16)
+        return whitening ? opt_kernel_h<__nv_bfloat16, true>(H, tail) : opt_kernel_h<__nv_bfloat16, false>(H, tail);
     return nullptr;
 }
 

@@ -86,7 +86,7 @@ def opt_case(hs, o, spectra, H, mitigation=True, dtype=0, w=None, per_spec_norm=
     return near, out
 
 
-@pytest.mark.parametrize("H", [1, 2, 7, 16, 31, 32])
+@pytest.mark.parametrize("H", [1, 2, 7, 8, 16, 31, 32])
 @pytest.mark.parametrize("mitigation", [True, False])
 def test_optimal_matches_oracle(hs, oracle_lib, H, mitigation):
     x = synth.spectrum(30001, 200 + H, [synth.Pulsar(211.37, 0.05), synth.Pulsar(97.9, 0.1)])
