@@ -223,7 +223,8 @@ void compute_tiles(hs_plan p)
     for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf_main[s] + T - 1) / T;
     p->tail_tile_start.assign(B + 1, 0);
     for (size_t s = 0; s < B; ++s)
-        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailThreads - 1) / kTailThreads;
+        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailThreads * kTailChains - 1) /
+                                                                 (kTailThreads * kTailChains);
     make_win_plan(p);
     make_chunks(p);
 }
