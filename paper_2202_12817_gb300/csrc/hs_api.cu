@@ -223,8 +223,7 @@ void compute_tiles(hs_plan p)
     for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf_main[s] + T - 1) / T;
     p->tail_tile_start.assign(B + 1, 0);
     for (size_t s = 0; s < B; ++s)
-        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailThreads * kTailChains - 1) /
-                                                                 (kTailThreads * kTailChains);
+        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailTile - 1) / kTailTile;
     make_win_plan(p);
     make_chunks(p);
 }

@@ -2,6 +2,7 @@
 #include "hs_fwd1d.cuh"
 #include "hs_fwd1d_win.cuh"
 #include "hs_fwd1d_pair.cuh"
+#include "hs_fwd1d_tail.cuh"
 
 namespace hs {
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel)

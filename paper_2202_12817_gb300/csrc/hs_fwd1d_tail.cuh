@@ -1,0 +1,174 @@
+// Truncated tail of the 1D forward (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1.
+#pragma once
+
+#include "hs_fwd1d.cuh"
+
+namespace hs {
+
+constexpr int kTailChains = 4;      // tail fundamentals per thread (a tile is kTailThreads x 4)
+constexpr int kTailAhead = 8;       // the tail prefetches the spectrum this many places ahead
+static_assert(kTailTile == kTailThreads * kTailChains, "host tail tiling and kernel chains disagree");
+
+// ---------------------------------------------------------------------------------------
+// kernel: the truncated tail (HS_FLAG_TRUNCATE_TAIL), fundamentals N_f <= n < N - 1 whose
+// higher orders would read past the end of the spectrum.  Each form keeps the orders whose
+// every possible read fits: simple h n <= N - 1, greedy h n + h <= N - 1 (drift at most h - 1
+// after order h - 1, plus the compared neighbour).  Both forms in one thread; a CTA per
+// kTailThreads x kTailChains consecutive tail fundamentals of one spectrum.
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
+{
+    // Truncated tail: fundamentals N_f <= n < N - 1, each form with the orders whose reads stay
+    // below N (simple h n <= N - 1, greedy h n + h <= N - 1).  Most of these fundamentals have a
+    // few orders only, so a thread's time is a short chain of dependent loads: each thread runs
+    // kTailChains fundamentals (n, n + T, ...) interleaved order by order to keep that many
+    // chains in flight.  Tiles run in decreasing spectrum order -- the main pass that precedes
+    // this kernel leaves the last spectra in L2 -- and the tiles of spectrum s bring spectrum
+    // s - kTailAhead into L2, one share each.
+    constexpr int CH = kTailChains;
+    __shared__ NormSmem nm;
+    __shared__ unsigned long long red[32];
+    constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
+    constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
+    const int H = a.H;
+    const int64_t tile = a.tail_tiles - 1 - static_cast<int64_t>(blockIdx.x);
+    const int s = tile_spectrum(a.tail_tile_start, a.B, tile);
+    const int64_t t0 = __ldg(a.tail_tile_start + s), t1 = __ldg(a.tail_tile_start + s + 1);
+    const int64_t fbase = __ldg(a.fund_off + s);
+    const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1
+    const int64_t len = __ldg(a.in_len + s);
+    const int64_t nbase = __ldg(a.nf_main + s) + (tile - t0) * (static_cast<int64_t>(blockDim.x) * CH) + threadIdx.x;
+    const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
+    const float *wv = a.w;
+    RunMax ms[CH], mg[CH];
+    uint32_t bits[CH], d[CH], n32[CH], hn[CH];
+    float ss[CH], sg[CH];
+    int Hs[CH], Hg[CH];
+    int Hmax = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int64_t n = nbase + static_cast<int64_t>(c) * blockDim.x;
+        ms[c] = RunMax{0.f, 1};
+        mg[c] = RunMax{0.f, 1};
+        bits[c] = 0;
+        d[c] = 0;
+        // orders of each form (n >= N_f >= 1 here); a fundamental past N - 2 takes no orders
+        const bool valid = n < nf;
+        const int64_t hs_ = valid ? (len - 1) / n : 0, hg_ = valid ? (len - 1) / (n + 1) : 0;
+        Hs[c] = kS ? static_cast<int>(hs_ < H ? hs_ : H) : 0;
+        Hg[c] = kG ? static_cast<int>(hg_ < H ? hg_ : H) : 0;
+        const int hm = Hs[c] > Hg[c] ? Hs[c] : Hg[c];
+        Hmax = hm > Hmax ? hm : Hmax;
+        n32[c] = valid ? static_cast<uint32_t>(n) : 0u;
+        hn[c] = n32[c];
+    }
+    // order 1 of every chain is loaded before the normalisation table, so the two latencies overlap
+    float x0[CH], x1[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        x0[c] = Hg[c] > 0 || Hs[c] > 0 ? ld_x<T, WHITEN>(x, wv, n32[c]) : 0.f;
+        x1[c] = (kG && a.mitigation && Hg[c] > 0) ? ld_x<T, WHITEN>(x, wv, n32[c] + 1) : x0[c];
+    }
+    const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
+    if (kS) load_norm(nm, 0, a.s.mu + no, a.s.sigma + no, H);
+    if (kG) load_norm(nm, 1, a.g.mu + no, a.g.sigma + no, H);
+    if (threadIdx.x == 0 && s >= kTailAhead) {
+        // share (t1 - 1 - tile) of spectrum s - kTailAhead, in 16-byte units
+        const int sp = s - kTailAhead;
+        const int64_t nb = __ldg(a.in_len + sp) * a.elem_bytes, nt = t1 - t0;
+        const int64_t chunk = ((nb + nt - 1) / nt + 15) & ~static_cast<int64_t>(15);
+        int64_t lo = (t1 - 1 - tile) * chunk;
+        const int64_t hi = lo + chunk < nb ? lo + chunk : nb;
+        const unsigned char *src = static_cast<const unsigned char *>(a.x) + __ldg(a.in_off + sp) * a.elem_bytes;
+        for (; lo + 16 <= hi; lo += 65536) {
+            const int64_t b = (hi - lo < 65536 ? hi - lo : 65536) & ~static_cast<int64_t>(15);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + lo), "r"(static_cast<uint32_t>(b)) : "memory");
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        ss[c] = x0[c];
+        sg[c] = x0[c];
+        if (kG && x1[c] > x0[c]) {
+            d[c] = 1;
+            sg[c] = x1[c];
+            bits[c] = 1u;
+        }
+        if (kS) ms[c].first(fmaf(ss[c], nm.rs[0][0], -nm.murs[0][0]));
+        if (kG) mg[c].first(fmaf(sg[c], nm.rs[1][0], -nm.murs[1][0]));
+    }
+    for (int h = 2; h <= Hmax; ++h) {
+        float vs[CH], va[CH], vb[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            hn[c] += n32[c];
+            if (kS && h <= Hs[c]) vs[c] = ld_x<T, WHITEN>(x, wv, hn[c]);
+            if (kG && h <= Hg[c]) {
+                va[c] = ld_x<T, WHITEN>(x, wv, hn[c] + d[c]);
+                vb[c] = ld_x<T, WHITEN>(x, wv, hn[c] + d[c] + 1);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (kS && h <= Hs[c]) {
+                ss[c] += vs[c];
+                ms[c].step(fmaf(ss[c], nm.rs[0][h - 1], -nm.murs[0][h - 1]), h);
+            }
+            if (kG && h <= Hg[c]) {
+                const bool inc = vb[c] > va[c];
+                sg[c] += inc ? vb[c] : va[c];
+                d[c] += inc;
+                bits[c] |= static_cast<uint32_t>(inc) << (h - 1);
+                mg[c].step(fmaf(sg[c], nm.rs[1][h - 1], -nm.murs[1][h - 1]), h);
+            }
+        }
+    }
+    unsigned long long ks = 0ull, kg = 0ull;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int64_t n = nbase + static_cast<int64_t>(c) * blockDim.x;
+        if (n >= nf) continue;
+        const int64_t o = fbase + n;
+        if (kS) {
+            a.s.snr[o] = ms[c].best;
+            a.s.best_h[o] = static_cast<uint8_t>(ms[c].bh);
+            const unsigned long long k = argmax_key(ms[c].best, n);
+            ks = k > ks ? k : ks;
+        }
+        if (kG) {
+            a.g.snr[o] = mg[c].best;
+            a.g.best_h[o] = static_cast<uint8_t>(mg[c].bh);
+            if (a.g.path) store_path(a.g.path, a.path_bytes, o, bits[c]);
+            const unsigned long long k = argmax_key(mg[c].best, n);
+            kg = k > kg ? k : kg;
+        }
+    }
+    if (kS && a.s.argmax) block_argmax(ks, a.s.argmax + s, red);
+    if (kG && a.g.argmax) {
+        if (kS && a.s.argmax) __syncthreads();
+        block_argmax(kg, a.g.argmax + s, red);
+    }
+}
+
+template <typename T>
+static const void *fwd1d_tail_kernel_for(int forms, int whitening)
+{
+    if (whitening) {
+        switch (forms) {
+        case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, true>);
+        case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 2, true>);
+        case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 3, true>);
+        }
+    } else {
+        switch (forms) {
+        case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, false>);
+        case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 2, false>);
+        case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 3, false>);
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace hs

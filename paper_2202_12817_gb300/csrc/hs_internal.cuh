@@ -144,8 +144,7 @@ const void *fwd1d_tail_kernel_f32(int forms, int whitening);
 const void *fwd1d_tail_kernel_f16(int forms, int whitening);
 const void *fwd1d_tail_kernel_bf16(int forms, int whitening);
 constexpr int kTailThreads = 256;
-constexpr int kTailChains = 4;      // truncated-tail fundamentals per thread (a tile is 1024)
-constexpr int kTailAhead = 8;       // the tail prefetches the spectrum this many places ahead
+constexpr int kTailTile = 1024;     // truncated-tail fundamentals per tile (kTailThreads x 4 per thread)
 const void *bwd1d_kernel(int form, int dtype, int whitening);
 const void *bwd_dw_reduce_kernel();
 const void *bwd_mark_kernel(int form);
