@@ -188,7 +188,8 @@ hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_for
  * needs the whole input), the argmax after the last chunk.  Ordered on `stream`: the copies
  * wait for work already enqueued there, and work enqueued after the call sees the outputs and
  * the host copies.  The first call creates the plan's two copy streams and their events; after
- * that no allocation and no synchronisation.  Calls on one plan must not overlap on the host. */
+ * that no allocation and no synchronisation, so later calls can be captured in a CUDA graph (each
+ * replay copies the buffers' current contents).  Calls on one plan must not overlap on the host. */
 hs_status hs_run_host(hs_plan plan, const void *host_spectra, void *spectra, const float *w,
                       const hs_form_io *simple, const hs_form_io *greedy, const hs_form_io *host_simple,
                       const hs_form_io *host_greedy, void *workspace, void *stream);

@@ -135,3 +135,37 @@ def test_rejects_same_buffer(hs):
     buf = torch.from_numpy(x).to(DEV)
     with pytest.raises(hs.HSError):
         hs.run_host(plan, buf, buf, None, None, out)
+
+
+def test_graph_capture_and_replay(hs):
+    """hs_run_host records into a CUDA graph (after a first call has created the plan's copy
+    streams and events); each replay copies the current contents of the pinned buffer."""
+    N, H = (1 << 22) + 11, 32
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=[N])
+    ns, ng = norms(hs, plan, 1), norms(hs, plan, 2)
+    out_s, out_g = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng)
+    host_s, host_g = plan.alloc_form_host(path=False), plan.alloc_form_host()
+    ref_s, ref_g = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng)
+    hbuf = torch.zeros(plan.extent, dtype=torch.float32).pin_memory()
+    dbuf = torch.zeros(plan.extent, dtype=torch.float32, device=DEV)
+    ws = plan.workspace(DEV)
+    side = torch.cuda.Stream(DEV)
+    with torch.cuda.stream(side):
+        hs.run_host(plan, hbuf, dbuf, None, out_s, out_g, host_s, host_g, ws, side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        hs.run_host(plan, hbuf, dbuf, None, out_s, out_g, host_s, host_g, ws, side)
+    for seed in (3, 4):
+        x = synth.spectrum(N, seed, synth.random_pulsars(3, N, seed + 10))
+        hbuf[:N] = torch.from_numpy(x)
+        g.replay()
+        torch.cuda.synchronize()
+        hs.run(plan, torch.from_numpy(x).to(DEV), None, ref_s, ref_g)
+        torch.cuda.synchronize()
+        for ref, out, host in ((ref_s, out_s, host_s), (ref_g, out_g, host_g)):
+            for field in ("snr", "best_h", "path", "argmax"):
+                r = getattr(ref, field)
+                if r is not None:
+                    same(r, getattr(out, field), f"replay {seed} {field}")
+                    same(r, getattr(host, field), f"replay {seed} {field} (host)")
