@@ -116,7 +116,9 @@ __device__ __forceinline__ void ld4(const void *p, int64_t j, int nv, float (&v)
 // when there is one group); k_bwd_dw_reduce then adds the groups in order.  Thread t owns bins
 // J + 4t .. J + 4t + 3 of the epilogue (L = 4 x blockDim.x) and keeps their dL/dw sum in registers.
 template <int FORM, typename T, bool WHITEN>
-__global__ void __launch_bounds__(256) k_bwd1d(const Bwd1DArgs a)
+// Four CTAs per SM (64 registers): the streaming epilogue needs the warps (0.376 ms vs 0.431 ms at
+// 78 registers and three CTAs on the 256 x 2^20 training step; five CTAs spill and take 0.526 ms).
+__global__ void __launch_bounds__(256, 4) k_bwd1d(const Bwd1DArgs a)
 {
     extern __shared__ __align__(16) unsigned char bsm[];
     const int L = a.block_bins;
