@@ -244,6 +244,13 @@ hs_status hs_run_fixed_scratch(hs_plan plan, const void *spectra, const float *w
 /* Synchronises `stream`, then reads and clears the plan's device error word. */
 hs_status hs_check_device_error(hs_plan plan, void *stream);
 
+/* Test of the bounded-wait path: enqueues one CTA that waits on a barrier phase that nothing
+ * completes, gives up after limit_us (1..1000000) microseconds and records the timeout in the
+ * plan's error word, as the kernels that wait on their own bulk copies do when a wait runs out
+ * (kernel 2, 1 s limit).  hs_check_device_error then returns HS_ERR_DEVICE_TIMEOUT; nothing is
+ * left in flight and the plan stays usable. */
+hs_status hs_selftest_timeout(hs_plan plan, uint32_t limit_us, void *stream);
+
 /* Host helper: closed-form mu/sigma ([H] each, host) of h-term partial sums when every summed
  * term is an independent draw from i.i.d. exponential noise of mean `mean1`: simple h mean1,
  * sqrt(h) mean1; greedy (mitigated) 1.5 h mean1, sqrt(1.25 h) mean1; greedy without mitigation

@@ -21,7 +21,7 @@ from . import _build
 
 __all__ = ["Plan", "FormIO", "Tuning", "HarmonicSum", "HSError", "run", "run_host", "run_fixed_scratch", "run_optimal", "backward",
            "norm_exponential", "OPTIMAL",
-           "check_device_error", "decode_argmax", "status_string", "SIMPLE", "GREEDY", "F32", "F16", "BF16",
+           "check_device_error", "selftest_timeout", "decode_argmax", "status_string", "SIMPLE", "GREEDY", "F32", "F16", "BF16",
            "FLAG_NO_MITIGATION", "FLAG_PER_SPECTRUM_NORM", "FLAG_WHITENING", "FLAG_AUTOTUNE", "FLAG_GRAPH",
            "FLAG_NO_DEVICE", "FLAG_CHECKED", "FLAG_TRUNCATE_TAIL", "lib", "LIB_PATH"]
 
@@ -103,6 +103,7 @@ def lib():
                                   ctypes.POINTER(_FormIO), ctypes.POINTER(_FormIO), _V, _V]
         L.hs_run_optimal.argtypes = [_V, _V, _V, ctypes.POINTER(_FormIO), _V]
         L.hs_check_device_error.argtypes = [_V, _V]
+        L.hs_selftest_timeout.argtypes = [_V, ctypes.c_uint32, _V]
         L.hs_norm_exponential.argtypes = [_I32, _I32, _I32, _I32, ctypes.c_double, _V, _V]
         L.hs_status_string.argtypes = [ctypes.c_int]
         L.hs_status_string.restype = ctypes.c_char_p
@@ -396,6 +397,12 @@ def backward(plan: Plan, form: int, grad_snr, fwd: FormIO, spectra=None, w=None,
 
 def check_device_error(plan: Plan, stream=None):
     _check(lib().hs_check_device_error(plan.handle, _stream_ptr(stream)), "device error")
+
+
+def selftest_timeout(plan: Plan, limit_us: int, stream=None):
+    """hs_selftest_timeout: run the bounded-wait path once (a wait that nothing completes gives up
+    after ``limit_us``); ``check_device_error`` then raises with HS_ERR_DEVICE_TIMEOUT."""
+    _check(lib().hs_selftest_timeout(plan.handle, int(limit_us), _stream_ptr(stream)), "hs_selftest_timeout")
 
 
 # ---------------------------------------------------------------------------------------------

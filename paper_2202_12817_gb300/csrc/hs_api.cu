@@ -1360,6 +1360,19 @@ hs_status hs_backward(hs_plan p, int32_t form, const float *grad_snr, const hs_f
     return HS_OK;
 }
 
+hs_status hs_selftest_timeout(hs_plan p, uint32_t limit_us, void *stream)
+{
+    if (!p) return HS_ERR_INVALID_ARG;
+    if (p->no_device) return HS_ERR_NO_DEVICE;
+    if (limit_us < 1 || limit_us > 1000000) return HS_ERR_INVALID_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return HS_ERR_CUDA;
+    unsigned long long limit_ns = 1000ull * limit_us;
+    void *args[] = {&p->d_err, &limit_ns};
+    HS_CUDA(cudaLaunchKernel(wait_selftest_kernel(), dim3(1), dim3(32), args, 0, static_cast<cudaStream_t>(stream)));
+    return HS_OK;
+}
+
 hs_status hs_check_device_error(hs_plan p, void *stream)
 {
     if (!p) return HS_ERR_INVALID_ARG;

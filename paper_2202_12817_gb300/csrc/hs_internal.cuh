@@ -138,6 +138,7 @@ const void *fwd1d_kernel_f32(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_f16(int forms, int whitening, int kernel);
 const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel(int dtype);
+const void *wait_selftest_kernel();
 const void *fwd1d_opt_kernel(int dtype, int whitening, int H, int tail);
 // 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 per CTA
 const void *fwd1d_tail_kernel_f32(int forms, int whitening);

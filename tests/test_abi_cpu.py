@@ -227,3 +227,10 @@ def test_tuning_2d_block_order(hs):
         with pytest.raises(hs.HSError):
             p.tuning = bad
     p.close()
+
+
+def test_selftest_timeout_needs_device(hs):
+    p = plan(hs, H=8, forms=hs.GREEDY, lengths=[1000])
+    with pytest.raises(hs.HSError) as e:
+        hs.selftest_timeout(p, 1000, stream=0)
+    assert e.value.status == 7     # HS_ERR_NO_DEVICE

@@ -248,3 +248,23 @@ def test_long_spectrum_full_size_pair(hs, oracle_lib, t):
     x = synth.long_spectrum()
     near = run_case(hs, oracle_lib, [x], 32, tuning=t)
     assert near <= 5
+
+
+@pytest.mark.parametrize("limit_us", [2000, 50000])
+def test_bounded_wait_reports_timeout(hs, oracle_lib, limit_us):
+    """A wait that nothing completes gives up after its limit and reports HS_ERR_DEVICE_TIMEOUT
+    through the plan's error word; the context and the plan stay usable afterwards."""
+    import time
+    x = synth.spectrum(20000, 5)
+    plan = hs.Plan(16, hs.SIMPLE | hs.GREEDY, lengths=[len(x)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs.selftest_timeout(plan, limit_us)
+    with pytest.raises(hs.HSError) as e:
+        hs.check_device_error(plan)
+    waited = time.perf_counter() - t0
+    assert e.value.status == 6                     # HS_ERR_DEVICE_TIMEOUT
+    assert waited >= limit_us * 1e-6 * 0.9 and waited < 5.0
+    hs.check_device_error(plan)                    # the error word was cleared
+    plan.close()
+    run_case(hs, oracle_lib, [x], 16)              # and the device still computes
