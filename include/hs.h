@@ -193,8 +193,10 @@ hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_for
 hs_status hs_run_host(hs_plan plan, const void *host_spectra, void *spectra, const float *w,
                       const hs_form_io *simple, const hs_form_io *greedy, const hs_form_io *host_simple,
                       const hs_form_io *host_greedy, void *workspace, void *stream);
-/* Chunks of hs_run_host's pipeline: 1..16, or 0 for the default (about 8 MiB of input per chunk,
- * at most 8).  A batch is cut between spectra, so it may get fewer chunks than asked for. */
+/* Chunks of hs_run_host's pipeline: 1..16, or 0 for the default (about 16 MiB of input per chunk,
+ * at most 8).  One spectrum is cut into chunks of decreasing size (K : K-1 : ... : 1 of its
+ * fundamentals), so the pass and output copies that follow the last input copy are short; a
+ * batch is cut between spectra, so it may get fewer chunks than asked for. */
 hs_status hs_plan_set_host_chunks(hs_plan plan, int32_t chunks);
 
 /* Forward pass of the optimal form (plan with HS_FORM_OPTIMAL, 1D): for every fundamental,

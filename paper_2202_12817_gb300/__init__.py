@@ -305,7 +305,7 @@ class Plan:
 
     @host_chunks.setter
     def host_chunks(self, k: int):
-        """Chunks of ``run_host``'s pipeline (0: about 8 MiB of input per chunk)."""
+        """Chunks of ``run_host``'s pipeline (0: about 16 MiB of input per chunk)."""
         _check(lib().hs_plan_set_host_chunks(self._h, int(k)), "hs_plan_set_host_chunks")
         self._host_chunks = int(k)
 

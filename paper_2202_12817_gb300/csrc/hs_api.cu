@@ -103,7 +103,7 @@ struct hs_plan_s {
     };
     std::vector<Chunk> chunks;
     bool chunk_out = false;      // outputs can be copied back chunk by chunk (no truncated tail)
-    int host_chunks = 0;         // requested chunk count (0: about 8 MiB of input per chunk)
+    int host_chunks = 0;         // requested chunk count (0: about 16 MiB of input per chunk)
     int64_t *d_chunk_tile_start = nullptr;
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr, ev_in[kMaxChunks] = {}, ev_out[kMaxChunks] = {};
@@ -161,7 +161,7 @@ void make_win_plan(hs_plan p);
 // Chunks of the pipelined host input (1D).  Fundamental n reads bins up to H n + H, so the
 // tiles ending at fundamental n_b need the input only up to H n_b + 1 (plus a margin for the
 // 16-byte-rounded window copies); one spectrum is cut into tile ranges, a batch into groups of
-// whole spectra.  By default about 8 MiB of input per chunk, at most 8 (hs_plan_set_host_chunks
+// whole spectra.  By default about 16 MiB of input per chunk, at most 8 (hs_plan_set_host_chunks
 // sets the count, up to kMaxChunks); a batch whose spectra do not lie in increasing order is one
 // chunk.
 void make_chunks(hs_plan p)
@@ -177,7 +177,7 @@ void make_chunks(hs_plan p)
     for (int64_t s = 0; s + 1 < B; ++s)
         if (p->in_off[s] + p->len[s] > p->in_off[s + 1]) ordered = false;
     const int64_t want = p->host_chunks > 0 ? p->host_chunks
-                                            : std::max<int64_t>(1, std::min<int64_t>(8, p->extent * eb / (8ll << 20)));
+                                            : std::max<int64_t>(1, std::min<int64_t>(8, p->extent * eb / (16ll << 20)));
     const int64_t K = ordered ? want : 1;
     const int64_t total = p->tile_start[B];
     if (K == 1 || total == 0) {
@@ -187,8 +187,12 @@ void make_chunks(hs_plan p)
     if (B == 1) {
         const int64_t base = p->in_off[0], len = p->len[0], nf = p->nf_main[0];
         int64_t lo = base;
+        // decreasing chunk sizes (K : K-1 : ... : 1): the last chunk, whose pass and output copies
+        // follow the last input copy, is the smallest
+        const int64_t wsum = K * (K + 1) / 2;
+        auto edge = [&](int64_t c) { return total * (c * K - c * (c - 1) / 2) / wsum; };   // sum of the first c weights
         for (int64_t c = 0; c < K; ++c) {
-            const int64_t t_a = total * c / K, t_b = total * (c + 1) / K;
+            const int64_t t_a = edge(c), t_b = edge(c + 1);
             if (t_b <= t_a) continue;
             const int64_t n_b = std::min(nf, t_b * T);
             int64_t need = c + 1 == K ? len : std::min(len, H * n_b + 1 + 32);

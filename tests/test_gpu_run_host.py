@@ -67,7 +67,7 @@ def check(hs, plan, buf, w=None, per_spec=False, mitigation=True):
 
 @pytest.mark.parametrize("chunks", [0, 1, 7, 16])
 def test_long_spectrum_chunks(hs, chunks):
-    """32 MiB: the default (four chunks of fundamentals) and other chunk counts, paired lanes."""
+    """32 MiB: the default (two chunks of fundamentals) and other chunk counts, paired lanes."""
     x = synth.long_spectrum()
     plan = hs.Plan(32, hs.SIMPLE | hs.GREEDY, lengths=[len(x)])
     plan.host_chunks = chunks
