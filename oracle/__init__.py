@@ -11,7 +11,8 @@ The arithmetic lives in ``hs_oracle.c`` (plain C, FP64, single thread), compiled
   simple_1d   Eq. 3 (simple harmonic sum) + Eq. 2 (SNR of partial sums, max over H)
   greedy_1d   Eq. 5 + Algorithm 2 (greedy drift tracking, optional fundamental comparison)
   greedy_2d   the 1D greedy rule lifted to a 3x3 f-fdot neighbourhood (the paper names the
-              higher-dimensional sum but gives no algorithm; this reading is stated in the design doc)
+              higher-dimensional sum but gives no algorithm: centre first, then the 8
+              neighbours in raster order, a strictly larger value replacing the best)
   backward_1d adjoint of the forward with the chosen path and best h held fixed
   dp_1d       optimal partial sums over all monotone drift paths (Sec. 2.2 drift tree)
   optimal_1d  dp_1d for every fundamental + Eq. 2's maximum over h (the optimal form)

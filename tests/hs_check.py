@@ -1,7 +1,7 @@
 """Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and compare it
 with the FP64 oracle.
 
-Comparison rules (the readings stated in the design doc):
+Comparison rules:
   * drift paths: bit-exact (comparisons are on stored values, exact in every dtype);
   * SNR: |snr_gpu - snr_ref| <= RTOL * (|S_ref| + |mu_h|) / sigma_h at the reference best h,
     i.e. 1e-5 relative to the un-cancelled magnitude (S_ref = snr_ref * sigma_h + mu_h);
@@ -15,7 +15,7 @@ RTOL = 1e-5
 
 
 def tol_at(ref_snr, bh, mu, sigma):
-    """amb-10 tolerance per fundamental (mu/sigma FP64 arrays [H] or [F, H])."""
+    """The SNR tolerance per fundamental (mu/sigma FP64 arrays [H] or [F, H])."""
     mu = np.asarray(mu, np.float64)
     sigma = np.asarray(sigma, np.float64)
     idx = bh.astype(np.int64) - 1
