@@ -84,6 +84,9 @@ def load_json(path):
         return None
 
 
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
+
+
 def measured_peaks():
     p = load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"))
     if p and "hbm_gbs" in p:
@@ -310,6 +313,7 @@ def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": pk.get("dram_bytes_per_launch") if fresh else None,
             "algorithmic_bytes": int(alg_bytes), "bytes_basis": how, "peak_kind": peak_kind,
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
             "kernel": pk.get("kernel") if fresh else None}
 
 
