@@ -169,3 +169,35 @@ def test_graph_capture_and_replay(hs):
                 if r is not None:
                     same(r, getattr(out, field), f"replay {seed} {field}")
                     same(r, getattr(host, field), f"replay {seed} {field} (host)")
+
+
+@pytest.mark.parametrize("H,lengths,dtype,chunks", [(1, [2], 0, 0), (8, [9], 0, 3), (8, [9, 10, 17], 1, 3),
+                                                    (32, [40001], 2, 5), (5, [(1 << 21) + 3], 1, 3)])
+def test_edge_shapes(hs, H, lengths, dtype, chunks):
+    """One fundamental (N = H + 1), H = 1, odd 16-bit lengths, several tiny spectra, more chunks
+    asked for than there are tiles."""
+    xs = [synth.spectrum(n, 60 + i) for i, n in enumerate(lengths)]
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=lengths, dtype=dtype)
+    plan.host_chunks = chunks
+    check(hs, plan, layout(plan, xs, dtype))
+
+
+def test_partial_host_outputs(hs):
+    """Host copies of some fields only (no path, no argmax, SNR only for the simple form)."""
+    N, H = (1 << 22) + 1, 16
+    x = synth.spectrum(N, 77, synth.random_pulsars(2, N, 78))
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=[N])
+    ns, ng = norms(hs, plan, 1), norms(hs, plan, 2)
+    ref_s, ref_g = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng)
+    dev = torch.from_numpy(x).to(DEV)
+    hs.run(plan, dev, None, ref_s, ref_g)
+    out_s, out_g = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng, path=False, argmax=False)
+    full_s = plan.alloc_form_host(path=False, argmax=False)
+    host_s = hs.FormIO(None, None, full_s.snr, None, None, None)
+    host_g = plan.alloc_form_host(path=True, argmax=True)
+    hs.run_host(plan, torch.from_numpy(x).pin_memory(), torch.empty_like(dev), None, out_s, out_g, host_s, host_g)
+    torch.cuda.synchronize()
+    same(ref_s.snr, host_s.snr, "simple snr")
+    same(ref_g.snr, host_g.snr, "greedy snr")
+    same(ref_g.best_h, host_g.best_h, "greedy best_h")
+    same(ref_g.snr, out_g.snr, "greedy snr (device)")
