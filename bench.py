@@ -271,14 +271,20 @@ def time_steps(torch, step, K, stream, flush=None):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def gather_ceiling():
+def gather_ceiling(device: int = 0, dist=None):
     """This GPU's L2 -> SM random-gather ceilings (line requests/s, sectors/s), measured live by
-    the probe program built next to libhs.so; None when it is missing or fails."""
+    the probe program built next to libhs.so on `device` (rank 0 only under torchrun); None when
+    it is missing or fails."""
+    if dist is not None and dist.get_rank() != 0:
+        return None
     exe = os.path.join(ROOT, "paper_2202_12817_gb300", "_build", "gather_probe")
     if not os.path.exists(exe):
         return None
     try:
-        r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        parts = [v for v in vis.split(",") if v.strip()] if vis else []
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES=parts[device] if device < len(parts) else str(device))
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=120, env=env)
         v = json.loads(r.stdout.strip().splitlines()[-1])
         return v if "line_requests_per_s" in v else None
     except Exception:
@@ -452,7 +458,7 @@ def wl_long(args, hs, torch, dev, world, dist):
                    "tuning": plan.tuning.as_dict()},
         "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "per_form": per_form,
-        "l2_gather": l2_gather_entry(wl, ms, plan.tuning.as_dict(), gather_ceiling()),
+        "l2_gather": l2_gather_entry(wl, ms, plan.tuning.as_dict(), gather_ceiling(dev.index, dist)),
         "warm_l2": {"value": world * units / (w_ms / 1e3), "unit": UNIT, "ms": round(w_ms, 5),
                     "note": "input left in L2 between steps (no flush): context, not the headline"},
         "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT,
