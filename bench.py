@@ -56,9 +56,9 @@ KERNEL_SOURCES = {
     "longbf16": ["hs_fwd1d.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_bf16.cu", "hs_internal.cuh"],
     "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
     "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
-    "plane": ["hs_fwd2d.cu"],
-    "plane16": ["hs_fwd2d.cu"],
-    "planebf16": ["hs_fwd2d.cu"],
+    "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
+    "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
+    "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
     "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
 }
 

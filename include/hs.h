@@ -156,13 +156,24 @@ hs_status hs_plan_input_offsets(hs_plan plan, int64_t *offsets);
 /* 2D fundamental domain: f in [f_lo, f_hi], z in [z_lo, z_hi]. */
 hs_status hs_plan_domain_2d(hs_plan plan, int64_t *f_lo, int64_t *f_hi, int64_t *z_lo, int64_t *z_hi);
 /* Bytes of device workspace hs_run / hs_backward take (0 = pass NULL): the forward's dynamic
- * schedule needs 256 bytes; the adjoint uses one partial dL/dw (N floats) per group of spectra
- * (up to 16 groups; required for a whitening plan with grad_w) followed by one byte per
- * (spectrum, 1024-bin block) that marks the blocks receiving contributions. */
+ * schedule needs 256 bytes; a 2D plane that admits the column sweep (kernel 2 below) adds 16
+ * bytes of chain state per fundamental it sweeps and 4 bytes per band; the adjoint uses one
+ * partial dL/dw (N floats) per group of spectra (up to 16 groups; required for a whitening plan
+ * with grad_w) followed by one byte per (spectrum, 1024-bin block) that marks the blocks
+ * receiving contributions. */
 hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
-/* Launch shape of the forward.  2D plans take only kernel 0 (CTAs over f-tiles fastest) or 1 (over
- * z rows fastest, the default: neighbouring z, whose low orders read overlapping rows, stay
- * co-resident), with threads = 256 and every other field 0. */
+/* Launch shape of the forward.  2D plans take kernel 0 (one thread per (f, z) chain, CTAs over
+ * f-tiles fastest) or 1 (the same over z rows fastest, the default: neighbouring z, whose low
+ * orders read overlapping rows, stay co-resident), with threads = 256 and every other field 0;
+ * or kernel 2, the column sweep: the plane is processed in bands of anchor columns h f, each
+ * band's columns of every reachable row staged in shared memory once by a 2D tensor copy and
+ * all orders of all chains anchored there run from it, the chain state waiting in the workspace
+ * between orders (plane DRAM reads about 2.4x lower than kernel 1 on a 201 x 2^21 plane).
+ * Kernel 2 takes threads 256, 512 or 1024 (two warps of which control and publish), stage_kb =
+ * band width / 16 (0: 64 columns for FP32, 96 for 16-bit storage), stages = 2..4 buffers (0: 2),
+ * ctas_per_sm 0..4; it needs rows whose byte stride is a multiple of 16, at most 256 reachable
+ * rows, no HS_FLAG_CHECKED, and the workspace (without one, hs_run and hs_run_fixed_scratch run
+ * it as kernel 1, with the same outputs bit for bit). */
 hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
 hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 

@@ -16,7 +16,7 @@ PROBE = os.path.join(BUILD, "gather_probe")
 
 # gather_probe.cu is a standalone measurement program, built separately (not part of libhs.so)
 SOURCES = ["hs_api.cu", "hs_fwd1d_f32.cu", "hs_fwd1d_f16.cu", "hs_fwd1d_bf16.cu", "hs_fwd1d_opt.cu", "hs_fwd2d.cu",
-           "hs_bwd1d.cu", "hs_selftest.cu"]
+           "hs_fwd2d_sweep.cu", "hs_bwd1d.cu", "hs_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                 "--expt-relaxed-constexpr"]

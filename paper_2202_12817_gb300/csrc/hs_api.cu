@@ -12,6 +12,9 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
+#include "hs_fwd2d_sweep.cuh"
 #include "hs_internal.cuh"
 
 using namespace hs;
@@ -121,8 +124,83 @@ int64_t tile_fund(const hs_desc &d, const hs_tuning &t)
     return static_cast<int64_t>(t.threads) * t.fund_per_thread;
 }
 
-// Forward: the dynamic schedule's tile counter (1D).
-size_t fwd_workspace_bytes(const hs_plan p) { return p->d.dims == 1 ? kWorkspaceBytes : 0; }
+// ---- 2D column sweep (kernel 2 of a 2D plan; schedule in hs_fwd2d_sweep.cuh) ----
+constexpr int kSweepStaticSmem = 3072;          // static shared memory of the sweep kernel (upper bound)
+constexpr int kSweepSmemLimit = 232448;         // 227 KiB opt-in per CTA
+constexpr int64_t kSweepPrefixBands = 64;       // chains f < 64 Wb run whole in the prefix tasks
+
+// Band width (anchor columns) when the tuning leaves it open: the two buffers (plane tile + the
+// band's chain state) of a ~200-row plane at H = 8 then take ~206 KB for FP32 (64 columns) and
+// ~209 KB for 16-bit storage (96 columns), one 512-thread CTA per SM.
+int sweep_default_wb(int dtype) { return dtype == HS_F32 ? 64 : 96; }
+
+struct SweepGeom {
+    bool ok = false;
+    int Wb = 0, r_lo = 0, nr = 0, box_bytes = 0, tile_bytes = 0, buf_bytes = 0, nbuf = 0;
+    int64_t f_s = 0, band_lo = 0, nbands = 0, n_prefix = 0;
+    size_t state_bytes = 0, sync_bytes = 0;
+};
+
+// Geometry of the sweep with band width Wb and `threads` per CTA; ok = false where the sweep
+// does not apply (checked plans, a row stride that is not a multiple of 16 bytes, more staged
+// rows than one tensor-copy box holds, tiles beyond shared memory, nothing beyond the prefix).
+SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2)
+{
+    SweepGeom g;
+    const hs_desc &d = p->d;
+    if (d.dims != 2 || (d.flags & HS_FLAG_CHECKED) || p->f_hi < p->f_lo || threads < 32 || threads % 32) return g;
+    const int eb = elem_bytes(d.dtype);
+    if (Wb < 16 || Wb % 16 || Wb + 2 * kSweepHalo > kSweepMaxBox) return g;
+    if ((d.n_freq * eb) % 16 || d.n_freq > (int64_t(1) << 30)) return g;
+    // rows a chain can read: z0 + h z +- h for z in [z_lo, z_hi], h = 1..H
+    const int64_t H = d.H;
+    int64_t rmin = d.z0_row + p->z_lo - 1, rmax = d.z0_row + p->z_hi + 1;
+    for (int64_t h = 2; h <= H; ++h) {
+        rmin = std::min(rmin, d.z0_row + h * p->z_lo - h);
+        rmax = std::max(rmax, d.z0_row + h * p->z_hi + h);
+    }
+    rmin = std::max<int64_t>(rmin, 0);
+    rmax = std::min<int64_t>(rmax, d.n_rows - 1);
+    const int64_t nr = rmax - rmin + 1;
+    if (nr < 3 || nr > kSweepMaxBox) return g;
+    const int64_t nz = p->z_hi - p->z_lo + 1;
+    const int64_t box = nr * (Wb + 2 * kSweepHalo) * eb;
+    const int64_t tile = (box + 127) / 128 * 128;
+    // a band holds at most ceil(Wb / h) chains of order h, each with nz states (orders >= 2)
+    int64_t state_cap = 0;
+    for (int64_t h = 2; h <= H; ++h) state_cap += (Wb + h - 1) / h * nz * 16;
+    const int64_t buf = (tile + state_cap + 127) / 128 * 128;
+    if (nbuf < 2 || nbuf > kSweepMaxStages || nbuf * buf + kSweepStaticSmem > kSweepSmemLimit) return g;
+    const int64_t f_s = std::max<int64_t>(p->f_lo, kSweepPrefixBands * Wb);
+    if (f_s > p->f_hi) return g;
+    const int compute = threads - 64;   // warps 0 and 1 control and publish
+    if (compute < 32) return g;
+    g.Wb = Wb;
+    g.r_lo = static_cast<int>(rmin);
+    g.nr = static_cast<int>(nr);
+    g.box_bytes = static_cast<int>(box);
+    g.tile_bytes = static_cast<int>(tile);
+    g.buf_bytes = static_cast<int>(buf);
+    g.nbuf = nbuf;
+    g.f_s = f_s;
+    g.band_lo = f_s / Wb;
+    g.nbands = H * p->f_hi / Wb - g.band_lo + 1;
+    g.n_prefix = ((f_s - p->f_lo) * nz + compute - 1) / compute;
+    g.state_bytes = static_cast<size_t>(nz * (p->f_hi - f_s + 1)) * 16;
+    g.sync_bytes = (static_cast<size_t>(2 + g.nbands) * 4 + 255) / 256 * 256;
+    g.ok = true;
+    return g;
+}
+
+// Forward workspace: the dynamic schedule's tile counter (1D); the sweep's chain state and band
+// flags (2D), sized for the narrowest band (16 columns: the most bands; any band width the sweep
+// can take, 16 can take too).
+size_t fwd_workspace_bytes(const hs_plan p)
+{
+    if (p->d.dims == 1) return kWorkspaceBytes;
+    const SweepGeom n = sweep_geom(p, 16, kSweepThreads);   // the most bands and the most sweep chains
+    return n.ok ? n.state_bytes + n.sync_bytes : 0;
+}
 
 // Adjoint with dL/dw: spectra are split into groups summed by different CTAs; each group's
 // partial dL/dw (N floats) lives in the workspace and a final pass adds them in order.
@@ -420,6 +498,97 @@ hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t 
     return HS_OK;
 }
 
+// The sweep kernel's dynamic shared-memory limit: the per-CTA opt-in maximum less its static
+// shared memory (set once per kernel).
+hs_status ensure_sweep_smem(const void *fn)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (std::find(g_attr_set.begin(), g_attr_set.end(), fn) != g_attr_set.end()) return HS_OK;
+    cudaFuncAttributes fa{};
+    HS_CUDA(cudaFuncGetAttributes(&fa, fn));
+    if (fa.sharedSizeBytes > static_cast<size_t>(kSweepStaticSmem)) return HS_ERR_UNSUPPORTED;
+    HS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSweepSmemLimit - static_cast<int>(fa.sharedSizeBytes)));
+    g_attr_set.push_back(fn);
+    return HS_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+// The 2D sweep: reset the ticket / band flags, describe the plane to the tensor copies, launch a
+// persistent grid.
+hs_status launch_sweep(const hs_plan p, const Fwd2DArgs &a, const SweepGeom &g, void *ws, cudaStream_t st)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return HS_ERR_UNSUPPORTED;
+    const int eb = elem_bytes(p->d.dtype);
+    const CUtensorMapDataType dt = p->d.dtype == HS_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : p->d.dtype == HS_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(p->d.n_freq), static_cast<cuuint64_t>(p->d.n_rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(p->d.n_freq) * eb};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(g.Wb + 2 * kSweepHalo), static_cast<cuuint32_t>(g.nr)};
+    const cuuint32_t estr[2] = {1, 1};
+    CUtensorMap map;
+    if (enc(&map, dt, 2, const_cast<void *>(a.plane), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return HS_ERR_CUDA;
+    Sweep2DArgs s{};
+    s.a = a;
+    s.f_s = g.f_s;
+    s.n_prefix = g.n_prefix;
+    s.band_lo = g.band_lo;
+    s.nbands = g.nbands;
+    s.Wb = g.Wb;
+    s.r_lo = g.r_lo;
+    s.nr = g.nr;
+    s.box_bytes = g.box_bytes;
+    s.tile_bytes = g.tile_bytes;
+    s.buf_bytes = g.buf_bytes;
+    s.nbuf = g.nbuf;
+    s.state = static_cast<int4 *>(ws);
+    s.sync = reinterpret_cast<unsigned *>(static_cast<uint8_t *>(ws) + g.state_bytes);
+    HS_CUDA(cudaMemsetAsync(s.sync, 0, sizeof(unsigned) * static_cast<size_t>(2 + g.nbands), st));
+    const void *fn = fwd2d_sweep_kernel(p->d.dtype);
+    if (!fn) return HS_ERR_UNSUPPORTED;
+    hs_status es = ensure_sweep_smem(fn);
+    if (es != HS_OK) return es;
+    const size_t smem = static_cast<size_t>(g.nbuf) * g.buf_bytes;
+    const int threads = p->tun.threads;
+    int per_sm = p->tun.ctas_per_sm;
+    if (per_sm <= 0) {
+        HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+        per_sm = std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>(static_cast<int64_t>(per_sm) * p->sms, g.n_prefix + g.nbands);
+    void *args[] = {&map, &s};
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(threads), args, smem, st));
+    return HS_OK;
+}
+
+// Band width of the sweep under the plan's tuning (stage_kb = width / 16; 0 = default) and its
+// buffers (stages; 0 = 2).
+int sweep_wb(const hs_plan p)
+{
+    return p->tun.stage_kb > 0 ? 16 * p->tun.stage_kb : sweep_default_wb(p->d.dtype);
+}
+int sweep_stages(const hs_plan p) { return p->tun.stages > 0 ? p->tun.stages : 2; }
+
 // Enqueue the forward pass (memsets + the main kernel + the truncated tail's) on `st`.
 // chunk >= 0 (1D): only the tiles of that chunk of the pipelined host input, on the tile prefix
 // shifted to its first tile, without the argmax reset (done once before the first chunk), the L2
@@ -444,10 +613,15 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         a.checked = (p->d.flags & HS_FLAG_CHECKED) ? 1 : 0;
         a.g = to_form_args(greedy);
         a.err = p->d_err;
+        if (p->tun.kernel == 2 && ws) {
+            const SweepGeom g = sweep_geom(p, sweep_wb(p), p->tun.threads, sweep_stages(p));
+            if (g.ok) return launch_sweep(p, a, g, ws, st);
+        }
+        // kernel 2 without a workspace runs as kernel 1 (the outputs are the same bit for bit)
         const int threads = 256;
         const int64_t ftiles = (a.nff + threads - 1) / threads;
         // tuning.kernel 1 (2D): z rows fastest, while the f-tiles fit in grid.y
-        a.zfast = (p->tun.kernel == 1 && ftiles <= 65535) ? 1 : 0;
+        a.zfast = (p->tun.kernel != 0 && ftiles <= 65535) ? 1 : 0;
         dim3 grid = a.zfast ? dim3(static_cast<unsigned>(a.nz), static_cast<unsigned>(ftiles))
                             : dim3(static_cast<unsigned>(ftiles), static_cast<unsigned>(a.nz));
         void *args[] = {&a};
@@ -746,6 +920,7 @@ hs_status check_run_args(const hs_plan p, const void *spectra, const float *w, c
     if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
     if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
     if (p->d.dims == 1 && p->tun.dynamic && (!workspace || !aligned(workspace, 8))) return HS_ERR_INVALID_ARG;
+    if (p->d.dims == 2 && workspace && !aligned(workspace, 16)) return HS_ERR_INVALID_ARG;
     return HS_OK;
 }
 
@@ -1060,10 +1235,21 @@ hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
 {
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->d.dims == 2) {
-        // 2D: kernel 0 = f-tiles fastest, 1 = z rows fastest; 256 threads, nothing else
-        if (!t || (t->kernel != 0 && t->kernel != 1) || t->threads != 256 || t->fund_per_thread != 1 ||
-            t->ctas_per_sm || t->dynamic || t->stages || t->stage_kb || t->prefetch || t->producers)
+        // 2D: kernel 0 = f-tiles fastest, 1 = z rows fastest (256 threads, nothing else);
+        // kernel 2 = the column sweep (256 or 512 threads, stage_kb = band width / 16, ctas_per_sm)
+        if (!t || t->kernel < 0 || t->kernel > 2 || t->fund_per_thread != 1 || t->dynamic || t->prefetch ||
+            t->producers)
             return HS_ERR_INVALID_ARG;
+        if (t->kernel < 2 && (t->threads != 256 || t->ctas_per_sm || t->stage_kb || t->stages))
+            return HS_ERR_INVALID_ARG;
+        if (t->kernel == 2) {
+            if ((t->threads != 256 && t->threads != 512 && t->threads != 1024) || t->ctas_per_sm < 0 || t->ctas_per_sm > 4 ||
+                t->stage_kb < 0 || t->stages < 0 || t->stages == 1 || t->stages > kSweepMaxStages)
+                return HS_ERR_INVALID_ARG;
+            const int wb = t->stage_kb > 0 ? 16 * t->stage_kb : sweep_default_wb(p->d.dtype);
+            const SweepGeom g = sweep_geom(p, wb, t->threads, t->stages > 0 ? t->stages : 2);
+            if (!g.ok || g.state_bytes + g.sync_bytes > fwd_workspace_bytes(p)) return HS_ERR_UNSUPPORTED;
+        }
         std::lock_guard<std::mutex> lk(p->mu);
         p->tun = *t;
         p->gvalid = false;
@@ -1434,7 +1620,8 @@ hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, c
 {
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
-    if (fwd_workspace_bytes(p) > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;   // more scratch than the array
+    // more scratch than the array (1D); a 2D plan runs without workspace (kernel 2 then runs as 1)
+    if (p->d.dims == 1 && fwd_workspace_bytes(p) > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;
     if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
     const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
     if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;
@@ -1449,7 +1636,8 @@ hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, c
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
     std::lock_guard<std::mutex> lk(p->mu);
-    return enqueue_fwd(p, spectra, w, simple, greedy, scratch, static_cast<cudaStream_t>(stream));
+    return enqueue_fwd(p, spectra, w, simple, greedy, p->d.dims == 1 ? scratch : nullptr,
+                       static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

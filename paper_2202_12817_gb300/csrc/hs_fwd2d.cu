@@ -1,11 +1,9 @@
-// 2D greedy harmonic sum over an f-fdot plane: the 1D greedy rule (Eq. 5, Algorithm 2)
-// lifted to a 3x3 neighbourhood at (h f + df, h z + dz).  The paper names the
-// higher-dimensional sum (acceleration search) without giving an algorithm; the rule here
-// is: best value starts at the centre, the 8 neighbours are scanned in raster order
-// (dz = -1..1 outer, df = -1..1 inner) and replace it only when strictly larger.
+// 2D greedy harmonic sum over an f-fdot plane, one thread per (f, z) chain carried in registers
+// through all orders (kernels 0 and 1 of the 2D plan); the per-order rule is chain2d_step.
 // The plane is stored as FP32, FP16 or BF16; each value is widened exactly to FP32, so the
 // comparisons are those of the stored values and the sum accumulates in FP32.
 #include "hs_fwd1d.cuh"
+#include "hs_fwd2d.cuh"
 
 namespace hs {
 
@@ -32,13 +30,10 @@ __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
     if (valid) {
         const int64_t f = a.f_lo + fi, z = a.z_lo + zi;
         const int64_t nfq = a.n_freq;
-        int64_t df = 0, dz = 0;
-        float sum = 0.f;
-        uint32_t bits = 0;
-        int bh = 1;
+        Chain2D c{0.f, 0.f, 0u, 0, 0, 1};
         for (int h = 1; h <= H; ++h) {
-            const int64_t cf = h * f + df;
-            const int64_t cr = a.z0_row + h * z + dz;
+            const int64_t cf = h * f + c.df;
+            const int64_t cr = a.z0_row + h * z + c.dz;
             if (a.checked) {
                 if (cr - 1 < 0 || cr + 1 > a.n_rows - 1 || cf - 1 < 0 || cf + 1 > nfq - 1) {
                     set_error(a.err, kErrBounds);
@@ -46,31 +41,17 @@ __global__ void __launch_bounds__(256) k_fwd2d(const Fwd2DArgs a)
                 }
             }
             const T *r0 = static_cast<const T *>(a.plane) + (cr - 1) * nfq + cf;   // row z - 1, column cf
-            const T *r1 = r0 + nfq;
-            const T *r2 = r1 + nfq;
-            const float c00 = ld_raw<T, int64_t>(r0, -1), c01 = ld_raw<T, int64_t>(r0, 0), c02 = ld_raw<T, int64_t>(r0, 1);
-            const float c10 = ld_raw<T, int64_t>(r1, -1), c11 = ld_raw<T, int64_t>(r1, 0), c12 = ld_raw<T, int64_t>(r1, 1);
-            const float c20 = ld_raw<T, int64_t>(r2, -1), c21 = ld_raw<T, int64_t>(r2, 0), c22 = ld_raw<T, int64_t>(r2, 1);
-            float v = c11;
-            int code = 4;
-            if (c00 > v) { v = c00; code = 0; }
-            if (c01 > v) { v = c01; code = 1; }
-            if (c02 > v) { v = c02; code = 2; }
-            if (c10 > v) { v = c10; code = 3; }
-            if (c12 > v) { v = c12; code = 5; }
-            if (c20 > v) { v = c20; code = 6; }
-            if (c21 > v) { v = c21; code = 7; }
-            if (c22 > v) { v = c22; code = 8; }
-            sum += v;
-            df += code % 3 - 1;
-            dz += code / 3 - 1;
-            bits |= static_cast<uint32_t>(code) << (4 * (h - 1));
-            const float snr = fmaf(sum, rs[h - 1], -murs[h - 1]);
-            if (h == 1 || snr > best) { best = snr; bh = h; }
+            float v9[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) v9[3 * r + q] = ld_raw<T, int64_t>(r0 + r * nfq, q - 1);
+            chain2d_step(c, h, v9, rs[h - 1], murs[h - 1]);
         }
+        best = c.best;
         a.g.snr[o] = best;
-        a.g.best_h[o] = static_cast<uint8_t>(bh);
-        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = bits;
+        a.g.best_h[o] = static_cast<uint8_t>(c.bh);
+        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = c.bits;
     }
     if (a.g.argmax) block_argmax(valid ? argmax_key(best, o) : 0ull, a.g.argmax, red);
 }

@@ -1,0 +1,459 @@
+// Column-sweep 2D greedy sum (kernel 2 of a 2D plan); the schedule is described in
+// hs_fwd2d_sweep.cuh, the per-order rule (shared with kernels 0 and 1) in hs_fwd2d.cuh.  Each
+// chain takes the same steps in the same order as in the register-resident kernel, so the
+// outputs are bit for bit those of kernels 0 and 1.
+#include "hs_fwd1d.cuh"
+#include "hs_fwd1d_win.cuh"
+#include "hs_fwd2d.cuh"
+#include "hs_fwd2d_sweep.cuh"
+
+namespace hs {
+namespace {
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 2D tensor copy of the box at (x, y) into shared memory, completing on `bar` (expect-tx).
+__device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                              uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// Chain state goes to L2 (bypassing L1); other CTAs read it back with bulk copies.
+__device__ __forceinline__ void st_state(int4 *p, int4 v)
+{
+    asm volatile("st.global.cg.v4.s32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync_id(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// state word w: best order | (df + 8) << 8 | (dz + 8) << 16   (|df|, |dz| <= H - 1 <= 7)
+__device__ __forceinline__ int4 pack_state(const Chain2D &c)
+{
+    return make_int4(__float_as_int(c.sum), __float_as_int(c.best), static_cast<int>(c.bits),
+                     c.bh | ((c.df + 8) << 8) | ((c.dz + 8) << 16));
+}
+
+__device__ __forceinline__ Chain2D unpack_state(int4 v)
+{
+    Chain2D c;
+    c.sum = __int_as_float(v.x);
+    c.best = __int_as_float(v.y);
+    c.bits = static_cast<uint32_t>(v.z);
+    c.bh = v.w & 0xff;
+    c.df = ((v.w >> 8) & 0xff) - 8;
+    c.dz = ((v.w >> 16) & 0xff) - 8;
+    return c;
+}
+
+// Bounded wait for phase `parity` of `bar`; false after kWaitNs or once another role has
+// reported a failure (`dead`).
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, volatile int *dead)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*dead) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// Named barrier `id` over n threads that returns the OR of every participant's predicate, so a
+// decision to stop is the same for all of them.
+__device__ __forceinline__ bool bar_or(int id, int n, bool pred)
+{
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<unsigned>(pred)), "r"(id), "r"(n)
+        : "memory");
+    return r != 0u;
+}
+
+// Push finished band jb (-1: no more) on the publisher's ring, waiting (bounded) while it is full.
+__device__ __forceinline__ void push_finished(int *ring, volatile unsigned &head, volatile unsigned &tail, int jb,
+                                              volatile int *dead, int *err)
+{
+    const unsigned h = head;
+    if (h - tail >= static_cast<unsigned>(kSweepRing)) {
+        const unsigned long long t0 = global_ns();
+        while (h - tail >= static_cast<unsigned>(kSweepRing)) {
+            if (*dead) return;
+            if (global_ns() - t0 > kWaitNs) { set_error(err, kErrTimeout); *dead = 1; return; }
+            __nanosleep(32);
+        }
+    }
+    ring[h % kSweepRing] = jb;
+    __threadfence_block();
+    head = h + 1;
+}
+
+// Per-buffer description of the task staged in it (written by the control warp before it
+// completes the buffer's `full` phase).
+struct BandHdr {
+    long long task;            // ticket; >= total: no more tasks
+    long long c0;              // first anchor column of the band
+    long long fa[kMaxH2D];     // order h = k + 1 holds chains [fa[k], fa[k] + nf[k]), all z
+    int nf[kMaxH2D];
+    int start[kMaxH2D + 1];    // first event of each order; start[H] = events of the band
+    int soff[kMaxH2D];         // int4 offset of order h's state segment in the buffer
+    float inv[kMaxH2D];        // 1 / nf (row split of the event index)
+};
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __grid_constant__ CUtensorMap tmap,
+                                                                   const Sweep2DArgs s)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ float rs[kMaxH2D], murs[kMaxH2D];
+    __shared__ unsigned long long red[32];
+    // full[b]: the plane tile and the chain state of buffer b's band have landed
+    __shared__ __align__(8) uint64_t full[kSweepMaxStages], empty[kSweepMaxStages];
+    __shared__ BandHdr hdr[kSweepMaxStages];
+    __shared__ int s_ring[kSweepRing];                  // finished bands, compute -> publisher
+    __shared__ volatile unsigned s_head, s_tail;        // ring entries pushed / published
+    __shared__ volatile int s_dead;
+
+    const Fwd2DArgs &a = s.a;
+    const int H = a.H, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nz = static_cast<int>(a.nz);
+    const int NC = blockDim.x - 64;                 // compute threads (warps 2..)
+    const long long total = s.n_prefix + s.nbands;
+    const int64_t f_hi = a.f_lo + a.nff - 1;
+    unsigned *ticket = s.sync, *done = s.sync + 2;  // done[j]: band j
+    if (tid < H) {
+        const float r = __frcp_rn(__ldg(a.g.sigma + tid));
+        rs[tid] = r;
+        murs[tid] = __fmul_rn(__ldg(a.g.mu + tid), r);
+    }
+    const int nbuf = s.nbuf;
+    if (tid == 0) {
+        for (int i = 0; i < nbuf; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        s_head = 0u;
+        s_tail = 0u;
+        s_dead = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned long long key = 0ull;   // best argmax key of this thread's finished chains
+
+    if (warp == 0) {
+        // ---- control warp: task k goes to buffer b = k % nbuf (free once the compute warps
+        // finished task k - nbuf).  Once the bands holding the previous orders of the band's
+        // chains are done it copies the band's plane tile and chain state into the buffer.
+        // Tickets are claimed one task ahead, and the next band's table is built and its
+        // dependency flags are read while the current band's copies are in flight.
+        const uint64_t pol_plane = l2_policy_evict_first();
+        const unsigned Wb = static_cast<unsigned>(s.Wb), band_lo = static_cast<unsigned>(s.band_lo);
+        const unsigned f_s = static_cast<unsigned>(s.f_s), f_end = static_cast<unsigned>(f_hi + 1);
+        unsigned pend = 0;                   // lane 0: buffers with copies not known to have landed
+        uint32_t last_use[kSweepMaxStages] = {0u, 0u, 0u, 0u};
+        auto claim = [&]() -> long long {
+            return lane == 0 ? (s_dead ? total : static_cast<long long>(atomicAdd(ticket, 1u))) : 0ll;
+        };
+        // the prepared band: lane h - 1 holds order h; lane 2 (h - 2) + i (i = 0, 1) the i-th band
+        // holding order h - 1 of order h's chains (p_dep = -1: none) with its flag as read
+        long long pt = 0;
+        unsigned p_fa = 0, p_nf = 0, p_flag = 1u;
+        int p_c0 = 0, p_inc = 0, p_sinc = 0, p_states = 0, p_dep = -1;
+        auto prepare = [&](long long t) {
+            pt = t;
+            p_nf = 0;
+            p_fa = 0;
+            p_dep = -1;
+            p_flag = 1u;
+            if (t < s.n_prefix || t >= total) return;
+            const unsigned j = static_cast<unsigned>(t - s.n_prefix);
+            const unsigned c0 = (band_lo + j) * Wb, c1 = c0 + Wb;
+            int dlo = 0, dhi = -1;
+            if (lane < H) {
+                const unsigned h = lane + 1;
+                unsigned fa = (c0 + h - 1) / h, fb = (c1 + h - 1) / h;
+                fa = fa > f_s ? fa : f_s;
+                fb = fb < f_end ? fb : f_end;
+                p_nf = fb > fa ? fb - fa : 0u;
+                p_fa = fa;
+                if (h > 1 && p_nf > 0) {
+                    dlo = static_cast<int>((h - 1) * fa / Wb - band_lo);
+                    dhi = static_cast<int>((h - 1) * (fb - 1) / Wb - band_lo);
+                }
+            }
+            const int cnt = static_cast<int>(p_nf) * nz, scnt = lane > 0 ? cnt : 0;
+            int inc = cnt, sinc = scnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o), w = __shfl_up_sync(0xffffffffu, sinc, o);
+                if (lane >= o) { inc += v; sinc += w; }
+            }
+            p_inc = inc;
+            p_sinc = sinc;
+            p_states = __shfl_sync(0xffffffffu, sinc, 31);
+            p_c0 = static_cast<int>(c0);
+            const int src = (lane >> 1) + 1 < kMaxH2D ? (lane >> 1) + 1 : 0;   // order h = src + 1 >= 2
+            const int lo = __shfl_sync(0xffffffffu, dlo, src), hi = __shfl_sync(0xffffffffu, dhi, src);
+            const int dep = lo + (lane & 1);
+            if (lane < 2 * (kMaxH2D - 1) && dep <= hi) {
+                if (dep < 0 || dep >= static_cast<int>(j)) set_error(a.err, kErrBounds);   // cannot happen, f_s >= Wb
+                else {
+                    p_dep = dep;
+                    p_flag = ld_acquire(done + dep);
+                }
+            }
+        };
+        {
+            long long t0 = claim();
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            prepare(t0);
+        }
+        long long t_next = claim();
+        for (long long k = 0;; ++k) {
+            const int b = static_cast<int>(k % nbuf);
+            const uint32_t u = static_cast<uint32_t>(k / nbuf);
+            if (k >= nbuf) {
+                int ok = 1;
+                if (lane == 0) ok = wait_phase(&empty[b], (u - 1) & 1u, &s_dead) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) { set_error(a.err, kErrTimeout); s_dead = 1; }
+                    break;
+                }
+                if (lane == 0) pend &= ~(1u << b);   // the compute warps waited on those copies
+            }
+            // one lane reads the failure flag, so the whole warp takes the same branch
+            const int dead = __shfl_sync(0xffffffffu, lane == 0 ? static_cast<int>(s_dead) : 0, 0);
+            const long long t = dead ? total : pt;
+            if (t >= total || t < s.n_prefix) {
+                if (lane == 0) {
+                    hdr[b].task = t;
+                    mbar_arrive(&full[b]);
+                }
+                if (t >= total) break;
+            } else {
+                const int cnt = static_cast<int>(p_nf) * nz, scnt = lane > 0 ? cnt : 0;
+                if (lane < H) {
+                    hdr[b].fa[lane] = p_fa;
+                    hdr[b].nf[lane] = static_cast<int>(p_nf);
+                    hdr[b].inv[lane] = p_nf > 0 ? __frcp_rn(static_cast<float>(p_nf)) : 0.f;
+                    hdr[b].start[lane] = p_inc - cnt;
+                    hdr[b].soff[lane] = p_sinc - scnt;
+                }
+                if (lane == H - 1) hdr[b].start[H] = p_inc;
+                if (lane == 0) {
+                    hdr[b].task = t;
+                    hdr[b].c0 = p_c0;
+                }
+                // dependencies: poll (bounded) the flags that were still clear when prepared; the
+                // bulk copies then read through the async proxy what other CTAs stored through the
+                // generic proxy, after the flags were acquired
+                if (p_dep >= 0 && p_flag == 0u) {
+                    const unsigned long long t0 = global_ns();
+                    while (ld_acquire(done + p_dep) == 0u) {
+                        if (*reinterpret_cast<volatile int *>(a.err) == kErrTimeout) break;
+                        if (global_ns() - t0 > kWaitNs) { set_error(a.err, kErrTimeout); break; }
+                        __nanosleep(64);
+                    }
+                }
+                __syncwarp();
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[b], static_cast<uint32_t>(s.box_bytes + 16 * p_states));
+                    tensor_g2s_2d(buf, &tmap, p_c0 - kSweepHalo, s.r_lo, &full[b], pol_plane);
+                    pend |= 1u << b;
+                    last_use[b] = u;
+                }
+                __syncwarp();
+                if (lane > 0 && lane < H && p_nf > 0)
+                    bulk_g2s(buf + s.tile_bytes + 16 * static_cast<size_t>(p_sinc - scnt),
+                             s.state + static_cast<long long>(p_fa - f_s) * nz, static_cast<uint32_t>(16 * cnt),
+                             &full[b]);
+            }
+            // the next task: its ticket was claimed one task ago
+            long long tn = __shfl_sync(0xffffffffu, t_next, 0);
+            if (tn < total) t_next = claim();
+            prepare(tn);
+        }
+        // copies of a buffer the compute warps never waited on (after a failure) land first
+        if (lane == 0)
+            for (int i = 0; i < nbuf; ++i)
+                if (pend & (1u << i)) {
+                    volatile int never = 0;
+                    wait_phase(&full[i], last_use[i] & 1u, &never);
+                }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- publisher: mark finished bands done.  The compute warps push each finished band on
+        // a shared ring; one GPU-scope fence then covers every band pushed so far (their state
+        // stores were ordered before the push by the compute warps' barrier), so a fence per
+        // batch rather than per band sets the flags.
+        if (lane == 0) {
+            unsigned tail = 0u;
+            bool end = false;
+            while (!end) {
+                unsigned head = s_head;
+                if (head == tail) {
+                    const unsigned long long t0 = global_ns();
+                    while ((head = s_head) == tail) {
+                        if (s_dead) break;
+                        if (global_ns() - t0 > kWaitNs) { set_error(a.err, kErrTimeout); s_dead = 1; break; }
+                        __nanosleep(32);
+                    }
+                    if (head == tail) break;
+                }
+                __threadfence();
+                for (; tail != head; ++tail) {
+                    const int jb = s_ring[tail % kSweepRing];
+                    if (jb < 0) { end = true; break; }
+                    st_release(done + jb, 1u);
+                }
+                s_tail = tail;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- compute warps: run task k from buffer k % nbuf, order by order
+        const int ctid = tid - 64;
+        const int P = s.Wb + 2 * kSweepHalo;
+        for (long long k = 0;; ++k) {
+            const int b = static_cast<int>(k % nbuf);
+            const uint32_t u = static_cast<uint32_t>(k / nbuf);
+            const bool lost = !wait_phase(&full[b], u & 1u, &s_dead);
+            if (bar_or(1, NC, lost)) {
+                if (ctid == 0) { set_error(a.err, kErrTimeout); s_dead = 1; }
+                break;
+            }
+            const BandHdr &hd = hdr[b];
+            const long long t = hd.task;
+            if (t >= total) {
+                if (ctid == 0) push_finished(s_ring, s_head, s_tail, -1, &s_dead, a.err);
+                break;
+            }
+            if (t < s.n_prefix) {
+                // prefix task: chains f < f_s, each carried in registers through all orders
+                const long long npf = s.f_s - a.f_lo;
+                const long long c = t * NC + ctid;
+                if (c < npf * nz) {
+                    const long long zi = c / npf, fi = c % npf;
+                    const long long f = a.f_lo + fi, z = a.z_lo + zi;
+                    Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
+                    for (int h = 1; h <= H; ++h) {
+                        const long long cf = h * f + ch.df, cr = a.z0_row + h * z + ch.dz;
+                        const T *r0 = static_cast<const T *>(a.plane) + (cr - 1) * a.n_freq + cf;
+                        float v9[9];
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) v9[3 * r + q] = ld_raw<T, int64_t>(r0 + r * a.n_freq, q - 1);
+                        chain2d_step(ch, h, v9, rs[h - 1], murs[h - 1]);
+                    }
+                    const long long o = zi * a.nff + fi;
+                    a.g.snr[o] = ch.best;
+                    a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
+                    if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
+                    const unsigned long long kk = argmax_key(ch.best, o);
+                    key = kk > key ? kk : key;
+                }
+                consumer_sync_id(1, NC);
+                if (ctid == 0) mbar_arrive(&empty[b]);
+                continue;
+            }
+            const int j = static_cast<int>(t - s.n_prefix);
+            const unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
+            const T *tile = reinterpret_cast<const T *>(buf);
+            const int4 *sst = reinterpret_cast<const int4 *>(buf + s.tile_bytes);
+            const int col0 = static_cast<int>(hd.c0 - kSweepHalo);   // plane column of tile column 0
+            // the band's events order by order (the per-order values are uniform across threads)
+            for (int h = 1; h <= H; ++h) {
+                const int nf = hd.nf[h - 1];
+                if (nf == 0) continue;
+                const int n = nf * nz, fa = static_cast<int>(hd.fa[h - 1]), so = hd.soff[h - 1];
+                const float inv = hd.inv[h - 1], rsh = rs[h - 1], mursh = murs[h - 1];
+                const int zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
+                for (int i = ctid; i < n; i += NC) {
+                    int zi = __float2int_rz((static_cast<float>(i) + 0.5f) * inv);
+                    if (zi * nf > i) --zi;
+                    else if ((zi + 1) * nf <= i) ++zi;
+                    const int fi = i - zi * nf;
+                    const int f = fa + fi;
+                    Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
+                    if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
+                    const int cf = h * f + ch.df;
+                    const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
+                    const T *p0 = tile + cr * P + (cf - 1 - col0);
+                    float v9[9];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
+                    chain2d_step(ch, h, v9, rsh, mursh);
+                    if (h == H) {
+                        const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
+                        a.g.snr[o] = ch.best;
+                        a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
+                        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
+                        const unsigned long long kx = argmax_key(ch.best, o);
+                        key = kx > key ? kx : key;
+                    } else {
+                        st_state(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
+                    }
+                }
+            }
+            // every compute thread is done with the buffer and has issued its stores: release the
+            // buffer to the control warp and hand the band to the publisher
+            consumer_sync_id(1, NC);
+            if (ctid == 0) {
+                mbar_arrive(&empty[b]);
+                push_finished(s_ring, s_head, s_tail, j, &s_dead, a.err);
+            }
+        }
+    }
+    __syncthreads();
+    if (a.g.argmax) block_argmax(key, a.g.argmax, red);
+}
+
+const void *fwd2d_sweep_kernel(int dtype)
+{
+    switch (dtype) {
+    case HS_F32: return reinterpret_cast<const void *>(&k_fwd2d_sweep<float>);
+    case HS_F16: return reinterpret_cast<const void *>(&k_fwd2d_sweep<__half>);
+    case HS_BF16: return reinterpret_cast<const void *>(&k_fwd2d_sweep<__nv_bfloat16>);
+    }
+    return nullptr;
+}
+
+}  // namespace hs

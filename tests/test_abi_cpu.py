@@ -217,8 +217,8 @@ def test_plan_create_without_gpu_fails_cleanly(hs):
 
 
 def test_tuning_2d_block_order(hs):
-    """2D plans take only the block order: kernel 0 (f-tiles fastest) or 1 (z rows fastest, the
-    default) with 256 threads."""
+    """Kernels 0 (f-tiles fastest) and 1 (z rows fastest, the default) take 256 threads and
+    nothing else; a plane too small for the column sweep refuses kernel 2."""
     p = hs.Plan(4, hs.GREEDY, dims=2, n_freq=1000, n_rows=41, z0_row=20, flags=hs.FLAG_NO_DEVICE)
     assert p.tuning.kernel == 1 and p.tuning.threads == 256
     p.tuning = dict(kernel=0, threads=256)
@@ -227,6 +227,39 @@ def test_tuning_2d_block_order(hs):
         with pytest.raises(hs.HSError):
             p.tuning = bad
     p.close()
+
+
+def test_tuning_2d_sweep(hs):
+    """The column sweep (kernel 2): its workspace holds 16 bytes of chain state per sweep chain
+    (f >= 64 x 16, the narrowest band) plus one flag per band; it takes 256, 512 or 1024 threads,
+    band widths that are multiples of 16 columns whose buffers fit in shared memory, 2..4 stages;
+    it is refused for checked plans and for rows whose byte stride is not a multiple of 16."""
+    n_freq, n_rows, z0, H = 1 << 21, 201, 100, 8
+    p = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=hs.FLAG_NO_DEVICE)
+    f_lo, f_hi, z_lo, z_hi = p.domain
+    nz, f_s = z_hi - z_lo + 1, 64 * 16
+    nbands = H * f_hi // 16 - f_s // 16 + 1
+    assert p.workspace_bytes == nz * (f_hi - f_s + 1) * 16 + (4 * (2 + nbands) + 255) // 256 * 256
+    assert p.tuning.kernel == 1                       # the sweep is opt-in
+    for ok in (dict(kernel=2, threads=512), dict(kernel=2, threads=256, stage_kb=2, stages=3),
+               dict(kernel=2, threads=1024, stage_kb=4, ctas_per_sm=1), dict(kernel=2, threads=512, stage_kb=1, stages=4)):
+        p.tuning = ok
+        assert p.tuning.kernel == 2
+    for bad in (dict(kernel=2, threads=128), dict(kernel=2, threads=512, stages=1), dict(kernel=2, threads=512, stages=5),
+                dict(kernel=2, threads=512, stage_kb=6), dict(kernel=2, threads=512, stage_kb=2, stages=4),
+                dict(kernel=2, threads=512, dynamic=1), dict(kernel=1, threads=256, stages=2)):
+        with pytest.raises(hs.HSError):
+            p.tuning = bad
+    p.close()
+    for kw in (dict(n_freq=n_freq + 1), dict(flags=hs.FLAG_CHECKED)):
+        args = dict(n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=0)
+        args.update(kw)
+        q = hs.Plan(H, hs.GREEDY, dims=2, n_freq=args["n_freq"], n_rows=n_rows, z0_row=z0,
+                    flags=hs.FLAG_NO_DEVICE | args["flags"])
+        assert q.workspace_bytes == 0
+        with pytest.raises(hs.HSError):
+            q.tuning = dict(kernel=2, threads=512)
+        q.close()
 
 
 def test_selftest_timeout_needs_device(hs):

@@ -13,9 +13,10 @@ DEV = torch.device("cuda", 0)
 # ---------------------------------------------------------------------------------------------
 # 2D greedy
 # ---------------------------------------------------------------------------------------------
-def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0):
+def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0, tuning=None):
     """dtype 1 / 2: the plane is rounded to FP16 / BF16 on the host (round to nearest even) and
-    the oracle runs on the rounded values, which FP32 holds exactly."""
+    the oracle runs on the rounded values, which FP32 holds exactly.  ``order`` picks kernel 0 or
+    1; ``tuning`` sets any launch shape (the column sweep: kernel 2)."""
     n_rows, n_freq = pl.shape
     if dtype:
         t = torch.from_numpy(pl).to({1: torch.float16, 2: torch.bfloat16}[dtype])
@@ -26,6 +27,9 @@ def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0):
     if order is not None:
         plan.tuning = dict(kernel=order, threads=256)     # 0: f-tiles fastest, 1: z rows fastest
         assert plan.tuning.kernel == order
+    if tuning is not None:
+        plan.tuning = tuning
+        assert plan.tuning.kernel == tuning["kernel"]
     assert plan.domain == o.domain_2d(n_freq, n_rows, z0, H)
     mu, sg = hs.norm_exponential(2, 2, H, True, mean1)
     ng = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
@@ -82,6 +86,8 @@ def test_2d_full_size(hs, oracle_lib):
     for order in (0, 1):
         near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, order=order)
         assert near <= 20
+    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, tuning=dict(kernel=2, threads=512))
+    assert near <= 20
     near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, dtype=1)
     assert near <= 20
 
