@@ -126,7 +126,6 @@ struct BandHdr {
     long long c0;              // first anchor column of the band
     long long fa[kMaxH2D];     // order h = k + 1 holds chains [fa[k], fa[k] + nf[k]), all z
     int nf[kMaxH2D];
-    int start[kMaxH2D + 1];    // first event of each order; start[H] = events of the band
     int soff[kMaxH2D];         // int4 offset of order h's state segment in the buffer
     float inv[kMaxH2D];        // 1 / nf (row split of the event index)
 };
@@ -190,7 +189,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         // holding order h - 1 of order h's chains (p_dep = -1: none) with its flag as read
         long long pt = 0;
         unsigned p_fa = 0, p_nf = 0, p_flag = 1u;
-        int p_c0 = 0, p_inc = 0, p_sinc = 0, p_states = 0, p_dep = -1;
+        int p_c0 = 0, p_sinc = 0, p_states = 0, p_dep = -1;
         auto prepare = [&](long long t) {
             pt = t;
             p_nf = 0;
@@ -213,14 +212,14 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     dhi = static_cast<int>((h - 1) * (fb - 1) / Wb - band_lo);
                 }
             }
-            const int cnt = static_cast<int>(p_nf) * nz, scnt = lane > 0 ? cnt : 0;
-            int inc = cnt, sinc = scnt;
+            // inclusive prefix over the orders of their state entries (orders >= 2)
+            const int scnt = lane > 0 ? static_cast<int>(p_nf) * nz : 0;
+            int sinc = scnt;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, inc, o), w = __shfl_up_sync(0xffffffffu, sinc, o);
-                if (lane >= o) { inc += v; sinc += w; }
+                const int w = __shfl_up_sync(0xffffffffu, sinc, o);
+                if (lane >= o) sinc += w;
             }
-            p_inc = inc;
             p_sinc = sinc;
             p_states = __shfl_sync(0xffffffffu, sinc, 31);
             p_c0 = static_cast<int>(c0);
@@ -269,10 +268,8 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     hdr[b].fa[lane] = p_fa;
                     hdr[b].nf[lane] = static_cast<int>(p_nf);
                     hdr[b].inv[lane] = p_nf > 0 ? __frcp_rn(static_cast<float>(p_nf)) : 0.f;
-                    hdr[b].start[lane] = p_inc - cnt;
                     hdr[b].soff[lane] = p_sinc - scnt;
                 }
-                if (lane == H - 1) hdr[b].start[H] = p_inc;
                 if (lane == 0) {
                     hdr[b].task = t;
                     hdr[b].c0 = p_c0;
