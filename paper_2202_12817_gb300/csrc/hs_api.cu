@@ -399,15 +399,24 @@ hs_status ensure_bwd_smem(const void *fn, size_t bytes)
     return HS_OK;
 }
 
+// Kernels whose dynamic shared-memory limit has been raised, per device (the attribute belongs to
+// the device the call is made on).
 std::mutex g_attr_mu;
-std::vector<const void *> g_attr_set;
+std::vector<std::pair<int, const void *>> g_attr_set;
+
+bool attr_is_set(const void *fn, int *device)
+{
+    if (cudaGetDevice(device) != cudaSuccess) *device = -1;
+    return std::find(g_attr_set.begin(), g_attr_set.end(), std::make_pair(*device, fn)) != g_attr_set.end();
+}
 
 hs_status ensure_dyn_smem(const void *fn)
 {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (std::find(g_attr_set.begin(), g_attr_set.end(), fn) != g_attr_set.end()) return HS_OK;
+    int dev = 0;
+    if (attr_is_set(fn, &dev)) return HS_OK;
     HS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-    g_attr_set.push_back(fn);
+    g_attr_set.emplace_back(dev, fn);
     return HS_OK;
 }
 
@@ -503,13 +512,14 @@ hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t 
 hs_status ensure_sweep_smem(const void *fn)
 {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (std::find(g_attr_set.begin(), g_attr_set.end(), fn) != g_attr_set.end()) return HS_OK;
+    int dev = 0;
+    if (attr_is_set(fn, &dev)) return HS_OK;
     cudaFuncAttributes fa{};
     HS_CUDA(cudaFuncGetAttributes(&fa, fn));
     if (fa.sharedSizeBytes > static_cast<size_t>(kSweepStaticSmem)) return HS_ERR_UNSUPPORTED;
     HS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSweepSmemLimit - static_cast<int>(fa.sharedSizeBytes)));
-    g_attr_set.push_back(fn);
+    g_attr_set.emplace_back(dev, fn);
     return HS_OK;
 }
 
