@@ -69,6 +69,8 @@ def lib():
             L.hso_simple_1d.argtypes = [_P, _P, _I32, _I64, _I32, _P, _P, _I64, _P, _P, _P]
             L.hso_greedy_1d.restype = ctypes.c_int
             L.hso_greedy_1d.argtypes = [_P, _P, _I32, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _P, _P]
+            L.hso_greedy_1d_list.restype = ctypes.c_int
+            L.hso_greedy_1d_list.argtypes = [_P, _P, _I32, _I64, _I32, _I32, _P, _P, _I64, _P, _P, _P, _P]
             L.hso_greedy_2d.restype = ctypes.c_int
             L.hso_greedy_2d.argtypes = [_P, _I64, _I64, _I64, _I32, _I64, _I64, _I64, _I64, _P, _P,
                                         _P, _P, _P, _P]
@@ -144,6 +146,22 @@ def greedy_1d(p, H, mu, sigma, mitigation=True, w=None, round_w=True, nf=None, w
                                _ptr(mu), _ptr(sigma), nf, _ptr(snr), _ptr(bh), _ptr(path), _ptr(allv)),
            "greedy_1d")
     return (snr, bh, path, allv) if want_all else (snr, bh, path)
+
+
+def greedy_1d_list(p, H, mu, sigma, fund, mitigation=True, w=None, round_w=True):
+    """Greedy HS of the listed fundamentals only.  Returns (snr, best_h, path) in list order."""
+    p = _f32(p)
+    w = _f32(w)
+    fund = np.ascontiguousarray(fund, np.int64)
+    cnt = fund.shape[0]
+    snr = np.empty(cnt, np.float64)
+    bh = np.empty(cnt, np.uint8)
+    path = np.empty(cnt, np.uint32)
+    mu, sigma = _f64(mu), _f64(sigma)
+    _check(lib().hso_greedy_1d_list(_ptr(p), _ptr(w), int(round_w), p.shape[0], int(H), int(bool(mitigation)),
+                                    _ptr(mu), _ptr(sigma), cnt, _ptr(fund), _ptr(snr), _ptr(bh), _ptr(path)),
+           "greedy_1d_list")
+    return snr, bh, path
 
 
 def domain_2d(n_freq, n_rows, z0_row, H):

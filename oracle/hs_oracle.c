@@ -81,39 +81,65 @@ int hso_simple_1d(const float *p, const float *w, int32_t round_w, int64_t n, in
  * Bit h-1 of path[n] records an increment at order h, so the bin chosen at order k is
  * k n + popcount(path & ((1 << k) - 1)).
  */
+static void greedy_one(const float *p, const float *w, int32_t round_w, int32_t H, int32_t mitigation,
+                       const double *mu, const double *sigma, int64_t f, double *snr, uint8_t *best_h,
+                       uint32_t *path, double *snr_all_row)
+{
+    int64_t d = 0;
+    uint32_t bits = 0;
+    double sum;
+    if (mitigation) {
+        double a = load_x(p, w, round_w, f), b = load_x(p, w, round_w, f + 1);
+        if (b > a) { d = 1; sum = b; bits |= 1u; }
+        else { sum = a; }
+    } else {
+        sum = load_x(p, w, round_w, f);
+    }
+    double best = snr_of(sum, 1, mu, sigma);
+    int bh = 1;
+    if (snr_all_row) snr_all_row[0] = best;
+    for (int h = 2; h <= H; ++h) {
+        int64_t m = (int64_t)h * f + d;
+        double a = load_x(p, w, round_w, m), b = load_x(p, w, round_w, m + 1);
+        if (b > a) { d += 1; sum += b; bits |= 1u << (h - 1); }
+        else { sum += a; }
+        double s = snr_of(sum, h, mu, sigma);
+        if (snr_all_row) snr_all_row[h - 1] = s;
+        if (s > best) { best = s; bh = h; }
+    }
+    if (snr) *snr = best;
+    if (best_h) *best_h = (uint8_t)bh;
+    if (path) *path = bits;
+}
+
 int hso_greedy_1d(const float *p, const float *w, int32_t round_w, int64_t n, int32_t H,
                   int32_t mitigation, const double *mu, const double *sigma, int64_t nf,
                   double *snr, uint8_t *best_h, uint32_t *path, double *snr_all)
 {
     if (!p || !mu || !sigma || H < 1 || H > HSO_MAX_H || nf < 0) return -1;
     if (nf > hso_nf_1d(n, H)) return -1;
-    for (int64_t f = 0; f < nf; ++f) {
-        int64_t d = 0;
-        uint32_t bits = 0;
-        double sum;
-        if (mitigation) {
-            double a = load_x(p, w, round_w, f), b = load_x(p, w, round_w, f + 1);
-            if (b > a) { d = 1; sum = b; bits |= 1u; }
-            else { sum = a; }
-        } else {
-            sum = load_x(p, w, round_w, f);
-        }
-        double best = snr_of(sum, 1, mu, sigma);
-        int bh = 1;
-        if (snr_all) snr_all[f * H] = best;
-        for (int h = 2; h <= H; ++h) {
-            int64_t m = (int64_t)h * f + d;
-            double a = load_x(p, w, round_w, m), b = load_x(p, w, round_w, m + 1);
-            if (b > a) { d += 1; sum += b; bits |= 1u << (h - 1); }
-            else { sum += a; }
-            double s = snr_of(sum, h, mu, sigma);
-            if (snr_all) snr_all[f * H + (h - 1)] = s;
-            if (s > best) { best = s; bh = h; }
-        }
-        if (snr) snr[f] = best;
-        if (best_h) best_h[f] = (uint8_t)bh;
-        if (path) path[f] = bits;
-    }
+    for (int64_t f = 0; f < nf; ++f)
+        greedy_one(p, w, round_w, H, mitigation, mu, sigma, f, snr ? snr + f : NULL, best_h ? best_h + f : NULL,
+                   path ? path + f : NULL, snr_all ? snr_all + f * H : NULL);
+    return 0;
+}
+
+/*
+ * The greedy form above for the `count` fundamentals listed in fund[] (each in [0, nf)), outputs
+ * in list order.  Used where only a few fundamentals can change, e.g. the fundamentals whose
+ * reads may include one perturbed bin in a finite-difference check.
+ */
+int hso_greedy_1d_list(const float *p, const float *w, int32_t round_w, int64_t n, int32_t H,
+                       int32_t mitigation, const double *mu, const double *sigma, int64_t count,
+                       const int64_t *fund, double *snr, uint8_t *best_h, uint32_t *path)
+{
+    if (!p || !mu || !sigma || !fund || H < 1 || H > HSO_MAX_H || count < 0) return -1;
+    const int64_t nf = hso_nf_1d(n, H);
+    for (int64_t i = 0; i < count; ++i)
+        if (fund[i] < 0 || fund[i] >= nf) return -1;
+    for (int64_t i = 0; i < count; ++i)
+        greedy_one(p, w, round_w, H, mitigation, mu, sigma, fund[i], snr ? snr + i : NULL,
+                   best_h ? best_h + i : NULL, path ? path + i : NULL, NULL);
     return 0;
 }
 

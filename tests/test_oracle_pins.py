@@ -343,6 +343,25 @@ def test_tail_pulse_train(oracle_lib):
         assert abs(allv[0, 19] - want) < 1e-9 and b[0] == 20
 
 
+def test_greedy_list_is_the_greedy_form_of_the_listed_fundamentals(oracle_lib):
+    """hso_greedy_1d_list runs the same per-fundamental steps as hso_greedy_1d, in list order,
+    with or without whitening and mitigation; a fundamental outside [0, N_f) is refused."""
+    o = oracle_lib
+    N, H = 5000, 13
+    x = synth.spectrum(N, 41, [synth.Pulsar(77.3, 0.05)])
+    w = synth.whitening(N, 3)
+    mu, sg = o.norm_exponential(2, 1, H)
+    nf = o.nf_1d(N, H)
+    fund = np.random.default_rng(2).integers(0, nf, 300)
+    for mit in (True, False):
+        for wv, rw in ((None, True), (w, True), (w, False)):
+            s, b, pa = o.greedy_1d(x, H, mu, sg, mitigation=mit, w=wv, round_w=rw)
+            s2, b2, p2 = o.greedy_1d_list(x, H, mu, sg, fund, mitigation=mit, w=wv, round_w=rw)
+            assert np.array_equal(s2, s[fund]) and np.array_equal(b2, b[fund]) and np.array_equal(p2, pa[fund])
+    with pytest.raises(ValueError):
+        o.greedy_1d_list(x, H, mu, sg, [nf])
+
+
 def test_path_invariants(oracle_lib):
     """d_m(h) = h-1 between fundamentals (Sec. 2.2); the fundamental comparison adds at most 1."""
     o = oracle_lib
@@ -532,6 +551,95 @@ def test_sector_footprint_2d(oracle_lib):
     path8 = o.greedy_2d(pl, z0, 3, *unit_norm(3))[2]
     c = o.sectors_2d(n_freq, n_rows, z0, 3, path8)
     assert 0 < c <= n_rows * n_freq // 8
+
+
+def _ramp_plane(n_freq, n_rows, sf, sz):
+    """Plane whose value strictly increases (s = +1) or decreases (s = -1) along f and z, or is
+    constant (s = 0 for both): values r n_freq + c are exact in float32 for these sizes."""
+    r = np.arange(n_rows, dtype=np.float64)[:, None]
+    c = np.arange(n_freq, dtype=np.float64)[None, :]
+    return (sz * r * n_freq + sf * c).astype(np.float32)
+
+
+# (sign along f, sign along z) -> the 3x3 offset every order takes: the largest neighbour is the
+# corner the ramp climbs towards; on a constant plane no neighbour is strictly larger than the
+# centre, so the centre is kept
+_RAMPS = [((1, 1), (1, 1)), ((-1, -1), (-1, -1)), ((1, -1), (1, -1)), ((-1, 1), (-1, 1)), ((0, 0), (0, 0))]
+
+
+@pytest.mark.parametrize("H", [2, 3, 5, 8])
+@pytest.mark.parametrize("signs,offset", _RAMPS)
+def test_sector_footprint_2d_along_known_paths(oracle_lib, H, signs, offset):
+    """On a ramp every order moves by the same 3x3 offset (of, oz), so the greedy path is known
+    without the oracle: code (oz + 1) * 3 + (of + 1) at every order, and order h is centred at
+    (h f + (h - 1) of, h z + (h - 1) oz).  The sector count must equal the number of distinct
+    32-byte sectors of the 3x3 neighbourhoods along those paths, listed here in Python."""
+    o = oracle_lib
+    n_freq, n_rows, z0 = 512, 57, 28
+    pl = _ramp_plane(n_freq, n_rows, *signs)
+    of, oz = offset
+    code = (oz + 1) * 3 + (of + 1)
+    f_lo, f_hi, z_lo, z_hi = o.domain_2d(n_freq, n_rows, z0, H)
+    path = o.greedy_2d(pl, z0, H, *unit_norm(H))[2]
+    want = sum(code << (4 * (h - 1)) for h in range(1, H + 1))
+    assert np.all(path == want)
+    per_row = -(-n_freq // 8)
+    sectors = set()
+    for z in range(z_lo, z_hi + 1):
+        for f in range(f_lo, f_hi + 1):
+            for h in range(1, H + 1):
+                cf, cr = h * f + (h - 1) * of, z0 + h * z + (h - 1) * oz
+                for a in (-1, 0, 1):
+                    for b in (-1, 0, 1):
+                        sectors.add((cr + a) * per_row + (cf + b) // 8)
+    assert o.sectors_2d(n_freq, n_rows, z0, H, path) == len(sectors)
+    # a sub-domain counts only its own fundamentals' reads
+    dom = (f_lo, min(f_hi, f_lo + 7), 0, 0)
+    sub = o.greedy_2d(pl, z0, H, *unit_norm(H), dom=dom)[2]
+    sec0 = set()
+    for f in range(dom[0], dom[1] + 1):
+        for h in range(1, H + 1):
+            cf, cr = h * f + (h - 1) * of, z0 + (h - 1) * oz
+            for a in (-1, 0, 1):
+                for b in (-1, 0, 1):
+                    sec0.add((cr + a) * per_row + (cf + b) // 8)
+    assert o.sectors_2d(n_freq, n_rows, z0, H, sub, dom=dom) == len(sec0)
+
+
+@pytest.mark.parametrize("signs,offset", _RAMPS)
+def test_2d_brute_force_best_sum_closed_form(oracle_lib, signs, offset):
+    """Exhaustive 2D enumeration on a ramp: the partial sum of h terms along any offset sequence
+    is sum_k value(z0 + k z + Dz_k, k f + Df_k) with D the running sum of the offsets, which the
+    ramp maximises by moving towards its top corner at every order.  So the best h-term sum is
+    that closed form (exact in FP64), exactly one sequence obeys the greedy rule, and it is the
+    all-(of, oz) path."""
+    o = oracle_lib
+    n_freq, n_rows, z0, H = 256, 41, 20, 5
+    pl = _ramp_plane(n_freq, n_rows, *signs)
+    sf, sz = signs
+    of, oz = offset
+    code = (oz + 1) * 3 + (of + 1)
+    f_lo, f_hi, z_lo, z_hi = o.domain_2d(n_freq, n_rows, z0, H)
+    for f, z in ((f_lo, z_lo), (f_hi, z_hi), ((f_lo + f_hi) // 2, 0), (f_lo + 3, z_hi - 1)):
+        best, rule_path, rule_count = o.brute_2d(pl, z0, H, f, z)
+        want, acc = [], 0.0
+        for k in range(1, H + 1):
+            r, c = z0 + k * z + k * oz, k * f + k * of
+            acc += sz * r * n_freq + sf * c
+            want.append(acc)
+        assert np.array_equal(best, np.array(want)), (f, z, best, want)
+        assert rule_count == 1
+        assert rule_path == sum(code << (4 * (h - 1)) for h in range(1, H + 1))
+    # a plane with one bright bin off the ramp's path: the optimum detours through it when that
+    # pays, so best_sum exceeds the greedy sum by exactly the detour's gain (here the bright bin
+    # sits at order 2 one column left of the greedy's (+1, +1) step on a constant plane)
+    flat = np.zeros((n_rows, n_freq), np.float32)
+    f, z = 10, 1
+    flat[z0 + 2 * z, 2 * f - 1] = 5.0          # reachable at order 2 only by offset (-1, 0)
+    best, rule_path, rule_count = o.brute_2d(flat, z0, H, f, z)
+    assert np.array_equal(best, np.array([0.0, 5.0, 5.0, 5.0, 5.0]))
+    # the greedy sees the bright bin in its order-2 neighbourhood and takes it
+    assert rule_count == 1 and ((rule_path >> 4) & 0xF) == 3
 
 
 def test_golden_footprints_match_oracle(oracle_lib):
