@@ -10,7 +10,7 @@ CUDA events on the stream hs_run launches on.
 Other workloads (--workload), each one JSON line of the same shape:
   long16 / longbf16   the same spectrum stored in FP16 / BF16 (FP32 accumulation)
   batch / batch16     2048 uneven spectra (2^20..2^23 bins), H = 16, 5 % with a pulsar, one
-                      persistent launch replayed from a CUDA graph, launch shape autotuned;
+                      launch replayed from a CUDA graph, launch shape autotuned (the line names it);
                       FP32 / FP16 storage (inputs 32 / 16 GB, larger than L2: no flush)
   plane               2D greedy over an f-fdot plane 201 x 2^21 (z = -100..100), H = 8,
                       chi-square(2) noise + 8 drifting signals (1.69 GB, larger than L2)
@@ -271,44 +271,6 @@ def time_steps(torch, step, K, stream, flush=None):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def gather_ceiling(device: int = 0, dist=None):
-    """This GPU's L2 -> SM random-gather ceilings (line requests/s, sectors/s), measured live by
-    the probe program built next to libhs.so on `device` (rank 0 only under torchrun); None when
-    it is missing or fails."""
-    if dist is not None and dist.get_rank() != 0:
-        return None
-    exe = os.path.join(ROOT, "paper_2202_12817_gb300", "_build", "gather_probe")
-    if not os.path.exists(exe):
-        return None
-    try:
-        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-        parts = [v for v in vis.split(",") if v.strip()] if vis else []
-        env = dict(os.environ, CUDA_VISIBLE_DEVICES=parts[device] if device < len(parts) else str(device))
-        r = subprocess.run([exe], capture_output=True, text=True, timeout=120, env=env)
-        v = json.loads(r.stdout.strip().splitlines()[-1])
-        return v if "line_requests_per_s" in v else None
-    except Exception:
-        return None
-
-
-def l2_gather_entry(wl, ms, tuning, probe):
-    """The timed kernel's L2 line requests and sectors per launch (from the committed ncu capture,
-    while the kernel's sources and launch shape are those captured) against the probe's ceilings."""
-    prof = (load_json(PROFILE_TRAFFIC) or {}).get(wl) or {}
-    if not probe or prof.get("kernel_hash") != kernel_hash(wl) or prof.get("tuning") != tuning:
-        return None
-    req, sec = prof.get("l2_requests_per_launch"), prof.get("l2_sectors_per_launch")
-    if not req or not sec:
-        return None
-    rq, sc = req / (ms / 1e3), sec / (ms / 1e3)
-    return {"requests_per_launch": req, "sectors_per_launch": sec,
-            "requests_per_s": rq, "requests_ceiling_per_s": probe["line_requests_per_s"],
-            "requests_frac": round(rq / probe["line_requests_per_s"], 4),
-            "sectors_per_s": sc, "sectors_ceiling_per_s": probe["sectors_per_s"],
-            "sectors_frac": round(sc / probe["sectors_per_s"], 4),
-            "note": "random-gather ceilings of this GPU measured by the gather probe (L2-resident buffer)"}
-
-
 def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
     """roofline entry; `traffic` = DRAM bytes per launch from the committed ncu capture of this
     workload, reported only while the kernel's sources and launch shape are those captured."""
@@ -321,6 +283,16 @@ def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
             "algorithmic_bytes": int(alg_bytes), "bytes_basis": how, "peak_kind": peak_kind,
             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
             "kernel": pk.get("kernel") if fresh else None}
+
+
+def launch_text(t):
+    """What one step launches, from the plan's (autotuned) launch shape."""
+    if t.get("ctas_per_sm", 0) > 0:
+        sched = "a persistent grid of %d CTAs per SM, %s" % (
+            t["ctas_per_sm"], "tiles from an atomic counter" if t.get("dynamic") else "tiles strided over the grid")
+    else:
+        sched = "one CTA per tile"
+    return "one launch of kernel %d (%s) replayed from a CUDA graph" % (t.get("kernel", 0), sched)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -458,7 +430,6 @@ def wl_long(args, hs, torch, dev, world, dist):
                    "tuning": plan.tuning.as_dict()},
         "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "per_form": per_form,
-        "l2_gather": l2_gather_entry(wl, ms, plan.tuning.as_dict(), gather_ceiling(dev.index, dist)),
         "warm_l2": {"value": world * units / (w_ms / 1e3), "unit": UNIT, "ms": round(w_ms, 5),
                     "note": "input left in L2 between steps (no flush): context, not the headline"},
         "e2e": {"value": world * units / (e_ms / 1e3), "unit": UNIT,
@@ -513,7 +484,7 @@ def wl_batch(args, hs, torch, dev, world, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == hs.F32 else "f16 storage, f32 accumulate",
         "data": "synthetic",
         "config": {"workload": f"{len(b.lengths)} uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
-                               "H=16, 5% with a pulsar, one persistent launch from a CUDA graph",
+                               f"H=16, 5% with a pulsar, {launch_text(plan.tuning.as_dict())}",
                    "bins": int(sum(b.lengths)), "H": H, "fundamentals": int(nf), "spectra": len(b.lengths),
                    "l2": "inputs larger than L2 (no flush)", "tuning": plan.tuning.as_dict()},
         "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how, plan.tuning.as_dict()),

@@ -12,9 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhs.so")
-PROBE = os.path.join(BUILD, "gather_probe")
 
-# gather_probe.cu is a standalone measurement program, built separately (not part of libhs.so)
 SOURCES = ["hs_api.cu", "hs_fwd1d_f32.cu", "hs_fwd1d_f16.cu", "hs_fwd1d_bf16.cu", "hs_fwd1d_opt.cu", "hs_fwd2d.cu",
            "hs_fwd2d_sweep.cu", "hs_bwd1d.cu", "hs_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,7 +34,7 @@ def _deps():
 
 
 def stale() -> bool:
-    if not os.path.exists(LIB) or not os.path.exists(PROBE):
+    if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _deps())
@@ -67,13 +65,6 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
-    # the L2 gather-ceiling probe bench.py reports beside the roofline (a standalone program)
-    probe_tmp = PROBE + f".tmp{os.getpid()}"
-    cmd = [nv, *ARCH, "-O3", "-std=c++17", os.path.join(CSRC, "gather_probe.cu"), "-o", probe_tmp]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed for gather_probe.cu:\n{r.stdout}\n{r.stderr}")
-    os.replace(probe_tmp, PROBE)
     return LIB
 
 
