@@ -245,8 +245,9 @@ hs_status hs_backward(hs_plan plan, int32_t form, const float *grad_snr, const h
  * tile counter of the dynamic schedule) is a fixed 4096-byte array inside the library, held on
  * every GPU that loads the library until the process exits.  Plans needing more workspace than
  * that get HS_ERR_UNSUPPORTED.  Nothing is allocated: no cudaMalloc, cudaFree or allocating
- * library call.  The first call on a device looks up the array's device address once (with
- * that device current); make that first call before any stream capture.  All calls share the
+ * library call.  Every call looks up the array's device address with the plan's device current
+ * (the address is not cached, so a device reset between calls is harmless); the first call on a
+ * device may load the library's device code, so make it before any stream capture.  All calls share the
  * one array and it keeps the last call's contents (the counter is cleared on the stream before
  * every launch), so calls whose work overlaps on the GPU -- on different streams, or of
  * different plans -- race and must be serialised by the caller.  HS_FLAG_GRAPH is ignored here

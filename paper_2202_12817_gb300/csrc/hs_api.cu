@@ -492,6 +492,46 @@ const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
     return nullptr;
 }
 
+// Clears the per-spectrum argmax keys of both forms and the dynamic schedule's tile counter before
+// a 1D pass.  Its first instruction lets the pass that follows it on the stream start at once
+// (programmatic dependent launch); the pass waits for this kernel only before its first argmax
+// update or tile-counter fetch, so the clear costs no serialisation gap.
+__global__ void k_fwd_reset(unsigned long long *s_key, unsigned long long *g_key, int64_t B,
+                            unsigned long long *counter)
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < B; i += stride) {
+        if (s_key) s_key[i] = 0ull;
+        if (g_key) g_key[i] = 0ull;
+    }
+    if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+}
+
+// Launch of a 1D forward kernel; with `after_reset` it may start while k_fwd_reset (enqueued just
+// before it) still runs -- every 1D forward kernel waits (griddepcontrol.wait) before it touches
+// what the reset writes.
+hs_status launch_fwd(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t st,
+                     bool after_reset)
+{
+    if (!after_reset) {
+        HS_CUDA(cudaLaunchKernel(fn, grid, block, args, smem, st));
+        return HS_OK;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HS_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return HS_OK;
+}
+
 // The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel.
 hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st)
 {
@@ -607,9 +647,8 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
                       const hs_form_io *greedy, void *ws, cudaStream_t st, int chunk = -1)
 {
     const int64_t B = p->d.dims == 1 ? p->d.num_spectra : 1;
-    if (chunk < 0 && simple && simple->argmax) HS_CUDA(cudaMemsetAsync(simple->argmax, 0, sizeof(uint64_t) * B, st));
-    if (chunk < 0 && greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t) * B, st));
     if (p->d.dims == 2) {
+        if (greedy && greedy->argmax) HS_CUDA(cudaMemsetAsync(greedy->argmax, 0, sizeof(uint64_t), st));
         Fwd2DArgs a{};
         a.plane = spectra;
         a.n_freq = p->d.n_freq;
@@ -673,6 +712,19 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     if ((p->d.forms & 3) == 0) return HS_OK;   // the optimal form runs through hs_run_optimal
     const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
     if (!fn) return HS_ERR_UNSUPPORTED;
+    // a whole pass clears the argmax keys (and the dynamic schedule's counter) with k_fwd_reset,
+    // which the pass may overlap; a chunk of hs_run_host relies on the clear before its first chunk
+    unsigned long long *s_key = simple ? reinterpret_cast<unsigned long long *>(simple->argmax) : nullptr;
+    unsigned long long *g_key = greedy ? reinterpret_cast<unsigned long long *>(greedy->argmax) : nullptr;
+    const bool dyn = t.kernel != 2 && t.dynamic && ws;
+    bool after_reset = false;
+    if (chunk < 0 && (s_key || g_key || dyn)) {
+        const int64_t rb = std::min<int64_t>(std::max<int64_t>((B + 255) / 256, 1), 64);
+        k_fwd_reset<<<static_cast<unsigned>(rb), 256, 0, st>>>(s_key, g_key, (s_key || g_key) ? B : 0,
+                                                              dyn ? static_cast<unsigned long long *>(ws) : nullptr);
+        HS_CUDA(cudaGetLastError());
+        after_reset = true;
+    }
     if (t.kernel == 2) {
         const size_t smem = static_cast<size_t>(p->wplan.nslot) * p->wplan.slot_bytes;
         hs_status es = ensure_dyn_smem(fn);
@@ -690,7 +742,8 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         if (chunk < 0 && (t.prefetch & 1) && p->l2_bytes > 0 && in_bytes <= p->l2_bytes / 4)
             wp.pf_chunk = ((in_bytes + grid - 1) / grid + 15) / 16 * 16;
         void *args[] = {&a, &wp};
-        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(block), args, smem, st));
+        hs_status ls = launch_fwd(fn, dim3(static_cast<unsigned>(grid)), dim3(block), args, smem, st, after_reset);
+        if (ls != HS_OK) return ls;
         return last ? launch_tail(p, a, st) : HS_OK;
     }
     int64_t grid = a.total_tiles;
@@ -706,13 +759,15 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     }
     if (t.dynamic) {
         a.tile_counter = static_cast<unsigned long long *>(ws);
-        // every CTA draws all of its tiles from this counter, starting at 0
-        HS_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), st));
+        // every CTA draws all of its tiles from this counter, starting at 0 (cleared by k_fwd_reset
+        // for a whole pass)
+        if (chunk >= 0) HS_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned long long), st));
     }
     if (grid > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     if (grid >= 1) {
         void *args[] = {&a};
-        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st));
+        hs_status ls = launch_fwd(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st, after_reset);
+        if (ls != HS_OK) return ls;
     }
     return last ? launch_tail(p, a, st) : HS_OK;
 }
@@ -1597,30 +1652,22 @@ hs_status hs_check_device_error(hs_plan p, void *stream)
 // them the scratch the forward needs (the tile counter of the dynamic schedule) lives in
 // the fixed array below, which the library's module holds on every GPU that loads it until
 // the process exits.  In host code `g_fixed_scratch` names a host-side stand-in, not a device
-// address, so its device address is looked up once per device (cudaGetSymbolAddress, with
-// that device current) and passed to the kernels.
+// address, so every call looks up its device address (cudaGetSymbolAddress, with the plan's
+// device current) and passes that to the kernels.  The lookup is not cached: a device reset or
+// a re-created primary context reloads the module at a new address, and a cached address would
+// then point at freed memory.
 // -----------------------------------------------------------------------------------------
 constexpr size_t kFixedScratchBytes = 4096;
 static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
 
 namespace {
-constexpr int kMaxFixedDevices = 64;
-std::mutex g_fixed_mu;
-void *g_fixed_ptr[kMaxFixedDevices] = {};
-
-// Device address of g_fixed_scratch on `device` (looked up on the first call for the device).
-hs_status fixed_scratch_ptr(int device, void **out)
+// Device address of g_fixed_scratch in the current context (the caller makes the device current).
+hs_status fixed_scratch_ptr(void **out)
 {
-    if (device < 0 || device >= kMaxFixedDevices) return HS_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_fixed_mu);
-    if (!g_fixed_ptr[device]) {
-        DeviceGuard guard(device);
-        if (!guard.ok) return HS_ERR_CUDA;
-        void *ptr = nullptr;
-        HS_CUDA(cudaGetSymbolAddress(&ptr, g_fixed_scratch));
-        g_fixed_ptr[device] = ptr;
-    }
-    *out = g_fixed_ptr[device];
+    void *ptr = nullptr;
+    HS_CUDA(cudaGetSymbolAddress(&ptr, g_fixed_scratch));
+    if (!ptr) return HS_ERR_CUDA;
+    *out = ptr;
     return HS_OK;
 }
 }  // namespace
@@ -1640,11 +1687,11 @@ hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, c
     if (want_s != (simple != nullptr) || want_g != (greedy != nullptr)) return HS_ERR_INVALID_ARG;
     if (simple) { hs_status st = check_io(p, simple, false); if (st != HS_OK) return st; }
     if (greedy) { hs_status st = check_io(p, greedy, true); if (st != HS_OK) return st; }
-    void *scratch = nullptr;
-    hs_status st = fixed_scratch_ptr(p->device, &scratch);
-    if (st != HS_OK) return st;
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
+    void *scratch = nullptr;
+    hs_status st = fixed_scratch_ptr(&scratch);
+    if (st != HS_OK) return st;
     std::lock_guard<std::mutex> lk(p->mu);
     return enqueue_fwd(p, spectra, w, simple, greedy, p->d.dims == 1 ? scratch : nullptr,
                        static_cast<cudaStream_t>(stream));

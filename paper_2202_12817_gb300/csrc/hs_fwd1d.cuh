@@ -77,6 +77,11 @@ __device__ __forceinline__ void set_error(int *err, int code)
     if (err) atomicCAS(err, kErrNone, code);
 }
 
+// Programmatic dependent launch: a 1D pass launched right after k_fwd_reset may start while that
+// kernel still clears the argmax keys and the tile counter; every access to those waits here
+// first.  Returns at once when the kernel was launched without the attribute or the reset is done.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Block-wide max of a 64-bit key, then one atomicMax per CTA.
 __device__ __forceinline__ void block_argmax(unsigned long long key, unsigned long long *dst,
                                              unsigned long long *scratch /*[32] smem*/)
@@ -95,7 +100,10 @@ __device__ __forceinline__ void block_argmax(unsigned long long key, unsigned lo
             unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
             key = k2 > key ? k2 : key;
         }
-        if (lane == 0 && key != 0ull) atomicMax(dst, key);
+        if (lane == 0 && key != 0ull) {
+            wait_prior_grid();
+            atomicMax(dst, key);
+        }
     }
 }
 
@@ -197,7 +205,10 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
 
     int64_t tile = blockIdx.x;
     if (a.tile_counter) {
-        if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+        if (threadIdx.x == 0) {
+            wait_prior_grid();
+            s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+        }
         __syncthreads();
         tile = s_tile;
     }

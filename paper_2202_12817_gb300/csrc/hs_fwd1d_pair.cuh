@@ -51,7 +51,10 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
     int loaded_spec = -1;
     int64_t tile = blockIdx.x;
     if (a.tile_counter) {
-        if (threadIdx.x == 0) s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+        if (threadIdx.x == 0) {
+            wait_prior_grid();
+            s_tile = static_cast<long long>(atomicAdd(a.tile_counter, 1ull));
+        }
         __syncthreads();
         tile = s_tile;
     }
@@ -156,7 +159,10 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
                     unsigned long long mx = 0ull;
                     for (int i = 0; i < static_cast<int>(blockDim.x >> 5); ++i)
                         mx = red[threadIdx.x][i] > mx ? red[threadIdx.x][i] : mx;
-                    if (mx != 0ull) atomicMax(dst + s, mx);
+                    if (mx != 0ull) {
+                        wait_prior_grid();
+                        atomicMax(dst + s, mx);
+                    }
                 }
             }
         }

@@ -128,7 +128,10 @@ __device__ __forceinline__ void consumer_argmax(unsigned long long key, unsigned
             unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
             key = k2 > key ? k2 : key;
         }
-        if (lane == 0 && key != 0ull) atomicMax(dst, key);
+        if (lane == 0 && key != 0ull) {
+            wait_prior_grid();
+            atomicMax(dst, key);
+        }
     }
     consumer_sync(nthreads);
 }
