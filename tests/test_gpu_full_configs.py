@@ -1,0 +1,184 @@
+"""GPU parity at the full sizes of the batched and the training workloads, in the launch
+configuration the benchmark times, against the FP64 oracle.
+
+* The batch: 2048 DM-trial spectra of uneven lengths (2^20..2^23 bins, 8.05e9 bins in all, more
+  than 2^32 input elements), H = 16, simple + greedy fused, one plan with the autotuned launch
+  shape replayed from a CUDA graph.  The oracle checks a seeded stratified sample of the trials:
+  every trial that carries a pulsar and 32 more per length class, element by element.
+* The training step: 256 spectra of 2^20 bins, H = 32, a learnable per-bin whitening vector
+  (init 1.0), greedy forward, loss = -(sum of the 16 largest SNRs per spectrum), adjoint to dL/dw.
+  Every spectrum's forward is compared with the oracle, dL/dw over the whole vector with the
+  oracle's analytic gradient, and on a 4096-bin slice holding pulsar harmonics with central
+  finite differences (eps = 1e-3) of the oracle's loss in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from hs_check import compare_argmax, compare_form, path_view
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+
+
+def _sample_trials(b, per_class=32, seed=91):
+    """Every pulsar trial plus `per_class` seeded trials of each length class."""
+    g = np.random.default_rng(seed)
+    pick = set(int(i) for i in b.pulsar_of)
+    for n in np.unique(b.lengths):
+        cls = [i for i in np.nonzero(b.lengths == n)[0] if int(i) not in pick]
+        pick.update(int(i) for i in g.choice(cls, size=min(per_class, len(cls)), replace=False))
+    return sorted(pick)
+
+
+@pytest.mark.parametrize("dtype", [0, 1], ids=["fp32", "fp16"])
+def test_batch_2048_trials_autotuned_graph_launch(hs, oracle_lib, dtype):
+    H = 16
+    b = synth.uneven_batch()
+    assert b.lengths.shape[0] == 2048 and b.total > 2 ** 32
+    x = synth.device_batch(b, DEV, dtype=torch.float16 if dtype == 1 else None)
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=b.lengths, dtype=dtype, offsets=b.offsets[:-1],
+                   flags=hs.FLAG_GRAPH | hs.FLAG_AUTOTUNE, device=0)
+    ns = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.SIMPLE, 1, H)]
+    ng = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
+    s_io = plan.alloc_form(*ns, path=False, argmax=True)
+    g_io = plan.alloc_form(*ng, path=True, argmax=True)
+    ws = plan.workspace(DEV)
+    stream = torch.cuda.current_stream(DEV)
+    hs.run(plan, x, None, s_io, g_io, ws, stream)
+    torch.cuda.synchronize()
+    first = [t.clone() for t in (s_io.snr, s_io.argmax, g_io.snr, g_io.path, g_io.argmax)]
+    hs.run(plan, x, None, s_io, g_io, ws, stream)      # second replay of the captured graph
+    torch.cuda.synchronize()
+    hs.check_device_error(plan)
+    for a, t in zip(first, (s_io.snr, s_io.argmax, g_io.snr, g_io.path, g_io.argmax)):
+        assert torch.equal(a, t), "graph replays differ"
+    del first
+    fo = plan.fund_offsets
+    mu_s, sg_s = [a.cpu().numpy() for a in ns]
+    mu_g, sg_g = [a.cpu().numpy() for a in ng]
+    trials = _sample_trials(b)
+    assert len(trials) >= 128 + len(b.pulsar_of) - 4
+    s_key, g_key = s_io.argmax.cpu().numpy(), g_io.argmax.cpu().numpy()
+    near = compared = 0
+    for i in trials:
+        off, n = int(b.offsets[i]), int(b.lengths[i])
+        xs = x[off:off + n].float().cpu().numpy()
+        a, e = int(fo[i]), int(fo[i + 1])
+        rs, rbh, rall = oracle_lib.simple_1d(xs, H, mu_s, sg_s, want_all=True)
+        gs, gbh, gpath, gall = oracle_lib.greedy_1d(xs, H, mu_g, sg_g, want_all=True)
+        assert e - a == rs.shape[0]
+        s_snr, s_bh = s_io.snr[a:e].cpu().numpy(), s_io.best_h[a:e].cpu().numpy()
+        g_snr, g_bh = g_io.snr[a:e].cpu().numpy(), g_io.best_h[a:e].cpu().numpy()
+        near += compare_form(s_snr, s_bh, rs, rbh, rall, mu_s, sg_s, what=f"trial {i} simple")
+        near += compare_form(g_snr, g_bh, gs, gbh, gall, mu_g, sg_g, path_view(g_io.path[a:e], H), gpath,
+                             what=f"trial {i} greedy")
+        compare_argmax(s_key[i], rs, s_snr, mu_s, sg_s, rbh, hs.decode_argmax, what=f"argmax {i} simple")
+        compare_argmax(g_key[i], gs, g_snr, mu_g, sg_g, gbh, hs.decode_argmax, what=f"argmax {i} greedy")
+        compared += 2 * (e - a)
+    # accepted near-ties (best h within the SNR tolerance of the reference's): rare on noise, more
+    # frequent with 16-bit storage, whose rounded values tie exactly more often
+    assert near <= 1e-4 * compared, (near, compared)
+    plan.close()
+
+
+def _candidates(j, H, nf):
+    """Fundamentals whose greedy reads can include bin j: order k reads bins k n .. k n + k."""
+    c = set()
+    for k in range(1, H + 1):
+        lo, hi = -(-(j - k) // k), j // k
+        c.update(range(max(lo, 0), min(hi, nf - 1) + 1))
+    return np.array(sorted(c), np.int64)
+
+
+def test_training_step_256x2p20_full_size(hs, oracle_lib):
+    B, N, H, K = 256, 1 << 20, 32, 16
+    p = torch.empty(B * N, dtype=torch.float32, device=DEV)
+    for i in range(B):
+        view = p[i * N:(i + 1) * N]
+        synth.device_noise(N, synth.SEED_BASE + 5 + 7 * i, DEV, out=view)
+        synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 5000 + i)[0]])
+    w = torch.ones(N, dtype=torch.float32, device=DEV, requires_grad=True)
+    plan = hs.Plan(H, hs.GREEDY, lengths=[N] * B, flags=hs.FLAG_WHITENING, device=0)
+    mu, sg = hs.norm_exponential(hs.GREEDY, 1, H)
+    nrm = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    snr, bh, path = hs.HarmonicSum.apply(p, w, plan, hs.GREEDY, *nrm)
+    nf = plan.total_fundamentals // B
+    top = snr.view(B, nf).topk(K, dim=1)
+    loss = -top.values.sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    gw = w.grad.cpu().numpy().astype(np.float64)
+    g_snr = snr.detach().view(B, nf).cpu().numpy()
+    g_bh = bh.view(B, nf).cpu().numpy()
+    g_path = path_view(path, H).reshape(B, nf)
+    g_top = top.indices.cpu().numpy()
+    ps = p.detach().view(B, N).cpu().numpy()
+
+    o = oracle_lib
+    gw_ref = np.zeros(N)
+    base = []
+    near = 0
+    for s in range(B):
+        rs, rbh, rpath, rall = o.greedy_1d(ps[s], H, mu, sg, want_all=True)
+        near += compare_form(g_snr[s], g_bh[s], rs, rbh, rall, mu, sg, g_path[s], rpath, what=f"spectrum {s}")
+        # the loss's discrete choice: the top 16 of the GPU's SNRs; the oracle's own top 16 agrees
+        # unless the 16th and 17th reference SNRs are within the SNR tolerance
+        order = np.argsort(-rs, kind="stable")
+        if set(order[:K]) != set(g_top[s]):
+            assert rs[order[K - 1]] - rs[order[K]] <= 1e-4, s
+        g = np.zeros(nf)
+        g[g_top[s]] = -1.0
+        gw_ref += ps[s].astype(np.float64) * o.backward_1d(2, N, H, rbh, sg, g, rpath)
+        base.append((rs, rbh, rpath, order[:K + 64]))
+    assert near <= 1e-4 * B * nf, near
+    np.testing.assert_allclose(gw, gw_ref, rtol=1e-5, atol=1e-6)
+
+    # central differences of the oracle's loss on the 4096-bin slice with the most bins that
+    # receive gradient (pulsar harmonics); only the fundamentals whose reads can include bin j
+    # change when w[j] moves, so they alone are recomputed
+    nz = np.nonzero(gw_ref)[0]
+    blocks = np.bincount(nz // 4096)
+    j0 = int(np.argmax(blocks)) * 4096
+    js = np.arange(j0, j0 + 4096)
+    hot = [int(j) for j in js if gw_ref[j] != 0.0]
+    hot = sorted(np.random.default_rng(17).choice(hot, size=min(256, len(hot)), replace=False).tolist())
+    sel = sorted(set(hot) | set(int(j) for j in js[::64]))
+    eps = 1e-3
+    w0 = np.ones(N, np.float32)
+    checked = flipped = 0
+    for j in sel:
+        cand = _candidates(j, H, nf)
+        losses, choices = [], []
+        for sign in (1.0, -1.0):
+            wv = w0.copy()
+            wv[j] += np.float32(sign * eps)
+            L, ch = 0.0, []
+            for s in range(B):
+                rs, rbh, rpath, top_more = base[s]
+                ns_, nb, npth = o.greedy_1d_list(ps[s], H, mu, sg, cand, w=wv, round_w=False)
+                vals = {int(n): rs[n] for n in top_more}
+                for n in cand:
+                    vals.pop(int(n), None)
+                vals.update({int(n): v for n, v in zip(cand, ns_)})
+                best = sorted(vals.items(), key=lambda kv: -kv[1])[:K]
+                L -= sum(v for _, v in best)
+                # the discrete choices the loss depends on: the top-16 set and the path and best h
+                # of those of its members that were recomputed (a flip in any other chain leaves
+                # the loss unchanged)
+                members = frozenset(n for n, _ in best)
+                ch.append((members, tuple((int(n), int(hb), int(pa)) for n, hb, pa in zip(cand, nb, npth)
+                                          if int(n) in members)))
+            losses.append(L)
+            choices.append(ch)
+        if choices[0] != choices[1]:
+            flipped += 1          # a choice the loss depends on flips inside +-eps: FD is no derivative there
+            continue
+        dw = float(np.float32(w0[j] + np.float32(eps))) - float(np.float32(w0[j] - np.float32(eps)))
+        fd = (losses[0] - losses[1]) / dw
+        assert abs(fd - gw[j]) <= 1e-4 * max(1.0, abs(fd)), (j, fd, gw[j])
+        checked += 1
+    assert checked >= 64 and flipped <= checked // 4, (checked, flipped)
+    plan.close()
