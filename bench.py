@@ -7,24 +7,33 @@ duty ~ U[0.02, 0.2)), 262143 fundamentals.  The spectrum (32 MiB) fits in L2, so
 (a write of max(2 x L2, 256 MiB)) before every timed step, and every step is timed alone with
 CUDA events on the stream hs_run launches on.
 
-Other workloads (--workload), each one JSON line of the same shape:
-  long16 / longbf16   the same spectrum stored in FP16 / BF16 (FP32 accumulation)
+The same line carries a ``workloads`` object with every other configuration, each timed in the
+same run with its own roofline, clocks and CPU baseline (``--extras none`` skips them):
   batch / batch16     2048 uneven spectra (2^20..2^23 bins), H = 16, 5 % with a pulsar, one
                       launch replayed from a CUDA graph, launch shape autotuned (the line names it);
                       FP32 / FP16 storage (inputs 32 / 16 GB, larger than L2: no flush)
-  plane               2D greedy over an f-fdot plane 201 x 2^21 (z = -100..100), H = 8,
-                      chi-square(2) noise + 8 drifting signals (1.69 GB, larger than L2)
-  table2              the paper's throughput configuration (Table 2): 1024 spectra x 131072 bins, H = 32,
-                      greedy; also with every bin a fundamental (truncated tail), in Gbin/s
+  plane / plane16     2D greedy over an f-fdot plane 201 x 2^21 (z = -100..100), H = 8,
+                      chi-square(2) noise + 8 drifting signals (1.69 GB FP32, larger than L2)
   grad                one training step of a learnable per-bin whitening: 256 spectra x 2^20
                       bins, H = 32, greedy forward, loss = -sum of the top-16 SNRs per spectrum
                       (torch.topk), hand-written adjoint to dL/dw
+  table2              the paper's throughput configuration (Table 2): 1024 spectra x 131072 bins, H = 32,
+                      greedy; also with every bin a fundamental (truncated tail), in Gbin/s
+Any of them (and long16 / longbf16, the headline spectrum in FP16 / BF16) can also be the
+headline of a run of its own (--workload).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ...]
+CPU baseline: the FP64 oracle on a bounded sample of the same input, on one thread (the oracle
+proper) and on every core of the host (the same source built with OpenMP over fundamentals,
+timed in a subprocess); ``cores`` is the thread count of ``value``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload ...] [--extras all|none]
     python bench.py --impl reference      # the FP64 oracle on the host cores, same metric
 
-N > 1 (torchrun): replicas only -- every rank runs the whole workload on its own GPU (the
-harmonic sum of one spectrum has no exchange step); value = units of all ranks / max time.
+N > 1 (torchrun): spectra of a batch (batch, batch16, table2, grad) are independent units, sharded
+over ranks longest-first with no data-path collective (per-spectrum argmax keys are gathered once
+after the timed steps); the training step all-reduces dL/dw (its one exchange) inside each step.
+One spectrum or one plane does not shard: every rank runs a replica.  value = units of all ranks /
+max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -192,6 +201,55 @@ def oracle_rate_2d(plane_host, z0_row, H, budget_s=8.0, z_rows=1):
             break
     units = reps * (f_hi - f_lo + 1) * z_rows * H
     return units / el, f"{reps} x z in [0, {z_rows}) x all {f_hi - f_lo + 1} f of the plane, 1 thread"
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate_all_cores(spec, budget_s):
+    """The oracle built with OpenMP over fundamentals, on every core of the host, in a subprocess
+    (its OpenMP runtime stays out of this process); None when that build is unavailable."""
+    import tempfile
+    threads = host_cores()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "input.npy")
+        np.save(path, spec["x"])
+        cmd = [sys.executable, "-m", "oracle.timing", "--input", path, "--dims", str(spec["dims"]),
+               "--H", str(spec["H"]), "--threads", str(threads), "--budget", str(budget_s)]
+        if spec["dims"] == 1:
+            cmd += ["--forms", str(spec.get("forms", 3)), "--frac", str(spec.get("frac", 1.0))]
+        else:
+            cmd += ["--z0", str(spec["z0"]), "--zrows", str(spec.get("zrows_all", 16))]
+        try:
+            r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=120 + 4 * budget_s)
+            return json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception as e:
+            log("all-core oracle timing failed:", e)
+            return None
+
+
+def cpu_baseline(spec, budget_one, budget_all):
+    """cpu_baseline object: value = the oracle on every host core (cores = its threads), with the
+    single-thread oracle beside it."""
+    if spec["dims"] == 1:
+        v1, s1 = oracle_rate_1d(spec["x"], spec["H"], budget_s=budget_one, frac=spec.get("frac", 1.0),
+                                forms=spec.get("forms", 3))
+    else:
+        v1, s1 = oracle_rate_2d(spec["x"], spec["z0"], spec["H"], budget_s=budget_one, z_rows=1)
+    one = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": s1}
+    allc = oracle_rate_all_cores(spec, budget_all)
+    if not allc or allc.get("threads", 1) <= 1:
+        out = dict(one)
+        out["cpu_model"] = allc.get("cpu") if allc else None
+        out["all_cores"] = None
+        return out
+    return {"value": allc["rate"], "unit": UNIT, "cores": int(allc["threads"]), "kind": "oracle",
+            "sample": allc["sample"] + " (the oracle's source built with OpenMP over fundamentals)",
+            "cpu_model": allc.get("cpu"), "single_thread": one}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -437,23 +495,30 @@ def wl_long(args, hs, torch, dev, world, dist):
                 "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in outs_h)),
                 "ms": round(e_ms, 5), "api": "hs_run_host (chunked copies overlapped with the pass)",
                 "copy_then_run": {"value": world * units / (s_ms / 1e3), "ms": round(s_ms, 5)}},
-        "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 3),
+        # per step: k_fwd_reset (argmax keys) + the fused pass
+        "gpu_launches": 2 * args.steps, "wall_s_timed_region": round(wall, 3),
     }
-    xs_host = x.float().cpu().numpy()
-    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0)
+    return result, clk.summary(), {"dims": 1, "x": x.float().cpu().numpy(), "H": H, "forms": 3}
 
 
 def wl_batch(args, hs, torch, dev, world, dist):
+    from paper_2202_12817_gb300 import dist as hsd
     H = 16
     dtype = hs.F16 if args.workload == "batch16" else hs.F32
     elem = 4 if dtype == hs.F32 else 2
     b = synth.uneven_batch(count=args.batch_spectra)
-    x = synth.device_batch(b, dev, dtype=torch.float16 if dtype == hs.F16 else None)
-    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=b.lengths, dtype=dtype, offsets=b.offsets[:-1],
+    B = len(b.lengths)
+    rank = dist.get_rank() if dist else 0
+    # N > 1: this rank's spectra (longest-processing-time shards), drawn and packed on its GPU
+    mine = hsd.shard_for_rank(b.lengths, world, rank) if world > 1 else list(range(B))
+    lb = synth.sub_batch(b, mine) if world > 1 else b
+    x = synth.device_batch(lb, dev, dtype=torch.float16 if dtype == hs.F16 else None)
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=lb.lengths, dtype=dtype, offsets=lb.offsets[:-1],
                    flags=hs.FLAG_GRAPH | (0 if args.tuning else hs.FLAG_AUTOTUNE), device=dev.index)
     if args.tuning:
         plan.tuning = json.loads(args.tuning)
     nf = plan.total_fundamentals
+    nf_all = int(sum((int(n) - 1) // H for n in b.lengths))
     ns = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.SIMPLE, 1, H)]
     ng = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
     s_io = plan.alloc_form(*ns, path=False, argmax=True)
@@ -461,8 +526,12 @@ def wl_batch(args, hs, torch, dev, world, dist):
     ws = plan.workspace(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def compute(idx):
         hs.run(plan, x, None, s_io, g_io, ws, stream)
+        return g_io.argmax.view(torch.int64)
+
+    def step():
+        hsd.batch_step(mine, B, compute, gather=False)
 
     for _ in range(args.warmup):
         step()
@@ -476,23 +545,33 @@ def wl_batch(args, hs, torch, dev, world, dist):
         wall = time.perf_counter() - t0
     ms = sum(times) / len(times)
     ms_max = max_over_ranks(ms, dist, dev)
+    gathered = None
+    if world > 1:
+        # the per-spectrum argmax keys of every rank, in global spectrum order (after the timed steps)
+        gathered = int(hsd.batch_step(mine, B, compute).shape[0])
     peak, peak_kind = measured_peaks()
-    alg, how = batch_alg_bytes(b.lengths, H, elem, nf)
+    alg, how = batch_alg_bytes(lb.lengths, H, elem, nf)
+    tun = plan.tuning.as_dict()
     result = {
-        "metric": METRIC, "value": world * nf * H / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": nf_all * H / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == hs.F32 else "f16 storage, f32 accumulate",
+        "scaling": "weak" if world == 1 else "strong",
+        "vs_baseline": None, "dtype": "f32" if dtype == hs.F32 else "f16 storage, f32 accumulate",
         "data": "synthetic",
-        "config": {"workload": f"{len(b.lengths)} uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
-                               f"H=16, 5% with a pulsar, {launch_text(plan.tuning.as_dict())}",
-                   "bins": int(sum(b.lengths)), "H": H, "fundamentals": int(nf), "spectra": len(b.lengths),
-                   "l2": "inputs larger than L2 (no flush)", "tuning": plan.tuning.as_dict()},
-        "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how, plan.tuning.as_dict()),
-        "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
+        "config": {"workload": f"{B} uneven spectra (2^20..2^23 bins, {'FP32' if dtype == hs.F32 else 'FP16'}), "
+                               f"H=16, 5% with a pulsar, {launch_text(tun)}",
+                   "bins": int(sum(b.lengths)), "H": H, "fundamentals": nf_all, "spectra": B,
+                   "parallelism": f"LPT shards over {world} ranks ({len(mine)} spectra on rank 0)" if world > 1
+                   else "1 GPU", "gathered_argmax_spectra": gathered,
+                   "l2": "inputs larger than L2 (no flush)", "tuning": tun},
+        "roofline": roofline(alg, ms, peak, peak_kind, args.workload, how, tun),
+        # per step: k_fwd_reset + the pass, replayed from one graph
+        "gpu_launches": 2 * steps, "wall_s_timed_region": round(wall, 3),
     }
-    i0 = int(np.argmax(b.lengths))
-    xs_host = synth.batch_trial(b, i0)
-    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0)
+    i0 = int(np.argmax(lb.lengths))
+    off = int(lb.offsets[i0])
+    xs_host = x[off:off + int(lb.lengths[i0])].float().cpu().numpy()
+    return result, clk.summary(), {"dims": 1, "x": xs_host, "H": H, "forms": 3}
 
 
 def wl_plane(args, hs, torch, dev, world, dist):
@@ -551,15 +630,19 @@ def wl_plane(args, hs, torch, dev, world, dist):
         "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }
-    host_plane = pl.float().cpu().numpy()
-    return result, clk.summary(), lambda: oracle_rate_2d(host_plane, synth.PLANE_Z0_ROW, H, budget_s=10.0)
+    return result, clk.summary(), {"dims": 2, "x": pl.float().cpu().numpy(), "H": H, "z0": synth.PLANE_Z0_ROW,
+                                   "zrows_all": 16}
 
 
 def wl_grad(args, hs, torch, dev, world, dist):
-    B, N, H, K = 256, 1 << 20, 32, 16
+    from paper_2202_12817_gb300 import dist as hsd
+    B_all, N, H, K = 256, 1 << 20, 32, 16
+    rank = dist.get_rank() if dist else 0
+    mine = hsd.shard_for_rank([N] * B_all, world, rank) if world > 1 else list(range(B_all))
+    B = len(mine)
     p = torch.empty(B * N, dtype=torch.float32, device=dev)
-    for i in range(B):
-        view = p[i * N:(i + 1) * N]
+    for k, i in enumerate(mine):
+        view = p[k * N:(k + 1) * N]
         synth.device_noise(N, synth.SEED_BASE + 5 + 7 * i, dev, out=view)
         synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 5000 + i)[0]])
     w = torch.ones(N, dtype=torch.float32, device=dev, requires_grad=True)
@@ -571,14 +654,27 @@ def wl_grad(args, hs, torch, dev, world, dist):
     stream = torch.cuda.current_stream(dev)
     fwd_t, bwd_t = [], []
 
+    def compute():
+        snr, bh, path = hs.HarmonicSum.apply(p, w, plan, hs.GREEDY, mu, sg)
+        loss = -snr.view(B, nf).topk(K, dim=1).values.sum()
+        return loss
+
     def step(timed=False):
         w.grad = None
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        snr, bh, path = hs.HarmonicSum.apply(p, w, plan, hs.GREEDY, mu, sg)
-        loss = -snr.view(B, nf).topk(K, dim=1).values.sum()
+        loss = compute()
         e1.record(stream)
-        loss.backward()
+
+        def local_grad():
+            loss.backward()
+            return w.grad
+
+        # N > 1: the step's one exchange, the sum of dL/dw over ranks
+        if world > 1:
+            hsd.grad_step(local_grad)
+        else:
+            local_grad()
         e2.record(stream)
         if timed:
             fwd_t.append((e0, e1))
@@ -600,38 +696,45 @@ def wl_grad(args, hs, torch, dev, world, dist):
     b_ms = sum(a.elapsed_time(b) for a, b in bwd_t) / steps
     ms = f_ms + b_ms
     ms_max = max_over_ranks(ms, dist, dev)
-    units = B * nf * H
+    units = B_all * nf * H
     peak, peak_kind = measured_peaks()
     frac = (load_json(GOLDEN) or {}).get("grad_H32_fraction", {}).get(str(N), {}).get("fused", 1.0)
     fwd_bytes = B * N * 4 * frac + N * 4 + B * nf * (4 + 1 + 4)
     bwd_bytes = B * N * 4 + B * nf * (4 + 1 + 4) + N * 4
     result = {
-        "metric": METRIC, "value": world * units / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": units / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak" if world == 1 else "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "training step: 256 spectra x 2^20 bins, H=32, learnable whitening, greedy "
-                               "forward + top-16 loss (torch.topk) + adjoint to dL/dw", "H": H, "spectra": B,
+                               "forward + top-16 loss (torch.topk) + adjoint to dL/dw", "H": H, "spectra": B_all,
+                   "parallelism": f"LPT shards over {world} ranks + all-reduce of dL/dw" if world > 1 else "1 GPU",
                    "fwd_ms": round(f_ms, 4), "bwd_ms": round(b_ms, 4), "l2": "inputs larger than L2 (no flush)",
                    "tuning": plan.tuning.as_dict()},
         "roofline": roofline(fwd_bytes + bwd_bytes, ms, peak, peak_kind, "grad",
                              "fwd: oracle sector fraction x input + w + outputs; bwd: input + forward outputs + dL/dw",
                              plan.tuning.as_dict()),
-        "gpu_launches": 2 * steps, "wall_s_timed_region": round(wall, 3),
+        # per step: the forward pass, the adjoint's marking pass, the adjoint and (spectra summed in
+        # more than one group) the reduction of the partial dL/dw
+        "gpu_launches": (3 + (1 if B > 1 else 0)) * steps, "wall_s_timed_region": round(wall, 3),
     }
-    xs_host = p[:N].cpu().numpy()
-    return result, clk.summary(), lambda: oracle_rate_1d(xs_host, H, budget_s=10.0, forms=2)
+    return result, clk.summary(), {"dims": 1, "x": p[:N].detach().cpu().numpy(), "H": H, "forms": 2}
 
 
 def wl_table2(args, hs, torch, dev, world, dist):
     """The paper's own throughput configuration (Table 2): 1024 FP32 power spectra of 131072 bins,
     H = 32, greedy form; Exp(1) noise, one pulsar in every spectrum.  Timed twice: over the fundamentals
     with all H orders, and with the truncated tail (every bin but the last a fundamental, the paper's
-    loop over all bins), whose fundamentals per second are the paper's "Gbin/s" under that reading."""
-    B, N, H = 1024, 1 << 17, 32
+    loop over all bins), whose fundamentals per second are the paper's "Gbin/s" under that reading.
+    N > 1: the spectra are sharded over the ranks."""
+    from paper_2202_12817_gb300 import dist as hsd
+    B_all, N, H = 1024, 1 << 17, 32
+    rank = dist.get_rank() if dist else 0
+    mine = hsd.shard_for_rank([N] * B_all, world, rank) if world > 1 else list(range(B_all))
+    B = len(mine)
     b = synth.Batch(np.full(B, N, np.int64), synth.pack_offsets(np.full(B, N, np.int64), 32), {}, synth.SEED_BASE + 6)
     x = torch.zeros(b.total, dtype=torch.float32, device=dev)
-    for i in range(B):
-        view = x[int(b.offsets[i]):int(b.offsets[i]) + N]
+    for k, i in enumerate(mine):
+        view = x[int(b.offsets[k]):int(b.offsets[k]) + N]
         synth.device_noise(N, synth.SEED_BASE + 6 + 13 * i, dev, out=view)
         synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 6000 + i)[0]])
     mu, sg = [torch.from_numpy(a).to(dev) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
@@ -642,9 +745,14 @@ def wl_table2(args, hs, torch, dev, world, dist):
         plan = hs.Plan(H, hs.GREEDY, lengths=b.lengths, offsets=b.offsets[:-1], flags=flags | hs.FLAG_AUTOTUNE,
                        device=dev.index)
         io = plan.alloc_form(mu, sg, path=True, argmax=True)
+        ws = None if not plan.workspace_bytes else plan.workspace(dev)
+
+        def compute(idx):
+            hs.run(plan, x, None, None, io, ws, stream)
+            return io.argmax.view(torch.int64)
 
         def step():
-            hs.run(plan, x, None, None, io, None if not plan.workspace_bytes else plan.workspace(dev), stream)
+            hsd.batch_step(mine, B_all, compute, gather=False)
 
         for _ in range(args.warmup):
             step()
@@ -655,33 +763,77 @@ def wl_table2(args, hs, torch, dev, world, dist):
         with ClockSampler(dev.index) as clk:
             times = time_steps(torch, step, steps, stream)
         clk_all = clk.summary() if clk_all is None else clk_all
-        ms = max_over_ranks(sum(times) / len(times), dist, dev)
-        out[name] = {"ms": ms, "fundamentals": plan.total_fundamentals, "tuning": plan.tuning.as_dict()}
+        ms_local = sum(times) / len(times)
+        ms = max_over_ranks(ms_local, dist, dev)
+        # fundamentals of all ranks: every spectrum has the same count
+        out[name] = {"ms": ms, "ms_local": ms_local, "fundamentals": plan.total_fundamentals // B * B_all,
+                     "tuning": plan.tuning.as_dict()}
         plan.close()
     m, a = out["main"], out["all_bins"]
     units = m["fundamentals"] * H
     peak, peak_kind = measured_peaks()
-    alg = B * N * 4 + m["fundamentals"] * (4 + 1 + 4) + 2 * 4 * H
+    alg = B * N * 4 + m["fundamentals"] // B_all * B * (4 + 1 + 4) + 2 * 4 * H
     result = {
-        "metric": METRIC, "value": world * units / (m["ms"] / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": units / (m["ms"] / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": min(args.steps, 100), "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak" if world == 1 else "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "the paper's Table 2 configuration: 1024 spectra x 131072 bins (FP32), H=32, greedy",
-                   "spectra": B, "bins": N, "H": H, "l2": "input (512 MiB) larger than L2 (no flush)",
-                   "gbin_per_s_full_harmonic_fundamentals": world * m["fundamentals"] / (m["ms"] / 1e3) / 1e9,
-                   "gbin_per_s_every_bin_truncated_tail": world * a["fundamentals"] / (a["ms"] / 1e3) / 1e9,
+                   "spectra": B_all, "bins": N, "H": H, "l2": "input (512 MiB) larger than L2 (no flush)",
+                   "parallelism": f"LPT shards over {world} ranks" if world > 1 else "1 GPU",
+                   "gbin_per_s_full_harmonic_fundamentals": m["fundamentals"] / (m["ms"] / 1e3) / 1e9,
+                   "gbin_per_s_every_bin_truncated_tail": a["fundamentals"] / (a["ms"] / 1e3) / 1e9,
                    "ms_every_bin_truncated_tail": a["ms"],
                    "paper_v100_greedy_gbin_per_s": 8.64,
                    "tuning": m["tuning"], "tuning_every_bin": a["tuning"]},
-        "roofline": roofline(alg, m["ms"], peak, peak_kind, "table2", "whole input + outputs", m["tuning"]),
-        "gpu_launches": min(args.steps, 100), 
+        "roofline": roofline(alg, m["ms_local"], peak, peak_kind, "table2", "whole input + outputs", m["tuning"]),
+        # per step: k_fwd_reset + the pass
+        "gpu_launches": 2 * min(args.steps, 100),
     }
-    xs_host = x[:N].cpu().numpy()
-    return result, clk_all, lambda: oracle_rate_1d(xs_host, H, budget_s=10.0, forms=2)
+    return result, clk_all, {"dims": 1, "x": x[:N].cpu().numpy(), "H": H, "forms": 2}
 
 
 WORKLOADS = {"long": wl_long, "long16": wl_long, "longbf16": wl_long, "batch": wl_batch, "batch16": wl_batch,
              "plane": wl_plane, "plane16": wl_plane, "planebf16": wl_plane, "grad": wl_grad, "table2": wl_table2}
+
+
+EXTRAS = ("batch", "batch16", "plane", "plane16", "grad", "table2")
+
+
+def reference_arm(args, rank, world):
+    """The FP64 oracle on the host cores (all of them where the OpenMP build of the oracle exists,
+    else one thread); each step runs the whole headline workload (one thread: 1/32 of its
+    fundamentals).  Under torchrun rank 0 alone runs it."""
+    if rank != 0:
+        return
+    import oracle
+    H = 32
+    x = synth.long_spectrum()
+    threads = host_cores()
+    if threads > 1:
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    omp = oracle.use_openmp(threads > 1)
+    threads = threads if omp else 1
+    nf = oracle.nf_1d(x.size, H)
+    frac = 1.0 if omp else 1.0 / 32
+    for _ in range(args.warmup):
+        oracle_rate_1d(x, H, budget_s=0.0, frac=frac / 4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate_1d(x, H, budget_s=0.0, frac=frac)
+    el = time.perf_counter() - t0
+    v = args.steps * int(nf * frac) * H / el
+    from oracle.timing import cpu_model
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "single spectrum of 2^23 bins (FP32), H=32, 16 pulsars, simple+greedy fused",
+                   "H": H},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"each step: fundamentals [0, {int(nf * frac)}) of the 2^23-bin spectrum, "
+                                   f"simple + greedy, FP64, {threads} thread(s)"
+                                   + (" (the oracle's source built with OpenMP over fundamentals)" if omp else "")},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 def main():
@@ -691,6 +843,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="long", choices=sorted(WORKLOADS))
+    ap.add_argument("--extras", default="all", choices=["all", "none"],
+                    help="with the headline workload, also time every other configuration (the line's "
+                         "'workloads' object)")
     ap.add_argument("--tuning", default=None, help="JSON hs_tuning override")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-spectra", type=int, default=2048,
@@ -700,46 +855,37 @@ def main():
     rank, world, local = dist_env()
 
     if args.impl == "reference":
-        # the FP64 oracle on the host cores, each step a bounded sample (1/32 of the fundamentals)
-        # of the default workload; under torchrun only rank 0 works
-        if rank != 0:
-            return
-        H = 32
-        x = synth.long_spectrum()
-        import oracle
-        nf = oracle.nf_1d(x.size, H)
-        frac = 1.0 / 32
-        for _ in range(args.warmup):
-            oracle_rate_1d(x, H, budget_s=0.0, frac=frac / 4)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            oracle_rate_1d(x, H, budget_s=0.0, frac=frac)
-        el = time.perf_counter() - t0
-        v = args.steps * int(nf * frac) * H / el
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "single spectrum of 2^23 bins (FP32), H=32, 16 pulsars, simple+greedy fused",
-                       "H": H},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: fundamentals [0, {int(nf * frac)}) of the 2^23-bin spectrum, "
-                                       "simple + greedy, single-thread FP64"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        reference_arm(args, rank, world)
         return
+
+    import copy
 
     import torch
     import paper_2202_12817_gb300 as hs
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     dist = init_dist(world, "nccl")
-    result, clocks, cpu_fn = WORKLOADS[args.workload](args, hs, torch, dev, world, dist)
+    result, clocks, cpu_spec = WORKLOADS[args.workload](args, hs, torch, dev, world, dist)
     result["clocks"] = clocks
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample = cpu_fn()
-        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
-    elif rank == 0:
-        result["cpu_baseline"] = None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    result["cpu_baseline"] = cpu_baseline(cpu_spec, 8.0, 5.0) if want_cpu else None
+    del cpu_spec
+    torch.cuda.empty_cache()
+    if args.workload == "long" and args.extras == "all" and not args.tuning:
+        extras = {}
+        for name in EXTRAS:
+            sub = copy.copy(args)
+            sub.workload = name
+            r, clk, spec = WORKLOADS[name](sub, hs, torch, dev, world, dist)
+            entry = {k: r[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "scaling", "dtype", "config",
+                                       "roofline", "gpu_launches")}
+            entry["clocks"] = clk
+            entry["cpu_baseline"] = cpu_baseline(spec, 3.0, 3.0) if want_cpu else None
+            extras[name] = entry
+            del r, spec
+            torch.cuda.synchronize(dev)
+            torch.cuda.empty_cache()
+        result["workloads"] = extras
     if rank == 0:
         print(json.dumps(result))
     if dist:

@@ -42,13 +42,23 @@ _lock = threading.Lock()
 _lib = None
 
 
+_FLAGS = ["-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math", "-ffp-contract=off"]
+LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (portable flags only: it also builds on the Arm GPU host)."""
+    """Compile liboracle.so with gcc (portable flags only: it also builds on the Arm GPU host),
+    and, where the compiler has OpenMP, liboracle_omp.so: the same source with its loops over
+    fundamentals spread over threads (the all-core CPU baseline; never used by the tests)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *_FLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = LIB_OMP + f".tmp{os.getpid()}"
+        r = subprocess.run(["gcc", *_FLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, LIB_OMP)
     return _LIB
 
 
@@ -57,12 +67,24 @@ _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
 
 
+_use_omp = False
+
+
+def use_openmp(on: bool = True) -> bool:
+    """Route every call to liboracle_omp.so (the all-core CPU baseline) instead of the
+    single-threaded oracle; call before the first oracle call.  False when that build is missing."""
+    global _use_omp
+    build()
+    _use_omp = bool(on) and os.path.exists(LIB_OMP)
+    return _use_omp
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
+            L = ctypes.CDLL(LIB_OMP if _use_omp else _LIB)
             L.hso_nf_1d.restype = _I64
             L.hso_nf_1d.argtypes = [_I64, _I32]
             L.hso_simple_1d.restype = ctypes.c_int

@@ -18,6 +18,12 @@
  *   mu[h-1], sigma[h-1]   mean and standard deviation of a partial sum of h terms (Eq. 2).
  *
  * Returns 0 on success, -1 on invalid arguments.
+ *
+ * The loops over fundamentals of the 1D simple and greedy forms and of the 2D form carry an
+ * OpenMP pragma.  The oracle proper (liboracle.so) is compiled without OpenMP, so the pragma is
+ * ignored and everything runs on one thread; the CPU baseline of the benchmark also times a
+ * second build with OpenMP (liboracle_omp.so), the same arithmetic spread over the host's cores
+ * (every fundamental is independent and writes only its own outputs).
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,6 +62,7 @@ int hso_simple_1d(const float *p, const float *w, int32_t round_w, int64_t n, in
 {
     if (!p || !mu || !sigma || H < 1 || H > HSO_MAX_H || nf < 0) return -1;
     if (nf > hso_nf_1d(n, H)) return -1;
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t f = 0; f < nf; ++f) {
         double sum = 0.0, best = 0.0;
         int bh = 0;
@@ -118,6 +125,7 @@ int hso_greedy_1d(const float *p, const float *w, int32_t round_w, int64_t n, in
 {
     if (!p || !mu || !sigma || H < 1 || H > HSO_MAX_H || nf < 0) return -1;
     if (nf > hso_nf_1d(n, H)) return -1;
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int64_t f = 0; f < nf; ++f)
         greedy_one(p, w, round_w, H, mitigation, mu, sigma, f, snr ? snr + f : NULL, best_h ? best_h + f : NULL,
                    path ? path + f : NULL, snr_all ? snr_all + f * H : NULL);
@@ -243,6 +251,7 @@ int hso_greedy_2d(const float *plane, int64_t n_freq, int64_t n_rows, int64_t z0
         if (z0_row + (int64_t)hh * z_hi + hh > n_rows - 1) return -1;
     }
     const int64_t nff = f_hi - f_lo + 1;
+#pragma omp parallel for collapse(2) schedule(dynamic, 1024)
     for (int64_t z = z_lo; z <= z_hi; ++z) {
         for (int64_t f = f_lo; f <= f_hi; ++f) {
             const int64_t o = (z - z_lo) * nff + (f - f_lo);

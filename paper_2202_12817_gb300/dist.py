@@ -5,7 +5,10 @@ bins up to H b + H), so a single spectrum or plane runs as independent replicas.
 independent spectra shard with no data-path collective:
 
   * ``lpt_shards`` assigns spectra to ranks longest-first (work is proportional to length),
-    deterministically, so every rank computes the same assignment without communicating;
+    deterministically, so every rank computes the same assignment without communicating
+    (``shard_for_rank`` is one rank's share);
+  * ``batch_step`` and ``grad_step`` are the steps the benchmark runs under torchrun, with the
+    per-rank compute passed in (the library's kernels on a GPU, the oracle in the CPU tests);
   * after each rank's forward, ``gather_by_spectrum`` collects per-spectrum results (e.g. the
     argmax keys) into global spectrum order on every rank;
   * the training step's only exchange is ``allreduce_sum`` of dL/dw over ranks (each rank's
@@ -41,6 +44,28 @@ def lpt_shards(lengths, world: int):
 def shard_loads(lengths, shards):
     lengths = np.asarray(lengths, dtype=np.int64)
     return [int(lengths[s].sum()) if s else 0 for s in shards]
+
+
+def shard_for_rank(lengths, world: int, rank: int):
+    """This rank's spectra under ``lpt_shards`` (sorted global indices)."""
+    return lpt_shards(lengths, world)[rank]
+
+
+def batch_step(mine, num_spectra: int, compute, group=None, gather: bool = True):
+    """One sharded forward over a batch: ``compute(mine)`` runs this rank's spectra and returns
+    their per-spectrum results (a tensor with one row per spectrum, in ``mine`` order), with no
+    collective; with ``gather`` they are then collected into global spectrum order on every rank."""
+    local = compute(mine)
+    if not gather:
+        return local
+    return gather_by_spectrum(local, mine, num_spectra, group)
+
+
+def grad_step(compute, group=None):
+    """One sharded training step: ``compute()`` runs forward, loss and adjoint over this rank's
+    spectra and returns its dL/dw (the sum over its spectra); the step's one exchange sums it
+    over ranks."""
+    return allreduce_sum(compute(), group)
 
 
 def gather_by_spectrum(local_values, my_indices, num_spectra: int, group=None):

@@ -123,10 +123,24 @@ class Batch:
     offsets: np.ndarray               # int64 [B+1] element offsets (aligned)
     pulsar_of: dict = field(default_factory=dict)   # trial -> Pulsar
     seed: int = 0
+    ids: np.ndarray | None = None     # trial k draws the noise of trial ids[k] of the full batch
 
     @property
     def total(self) -> int:
         return int(self.offsets[-1])
+
+    def trial_id(self, k: int) -> int:
+        return int(self.ids[k]) if self.ids is not None else int(k)
+
+
+def sub_batch(b: Batch, indices) -> Batch:
+    """Trials ``indices`` of ``b`` packed in that order (a rank's shard): trial k of the result
+    holds exactly trial indices[k] of ``b`` (same noise seed, same pulsar)."""
+    ids = np.asarray(indices, np.int64)
+    lengths = np.asarray(b.lengths, np.int64)[ids]
+    pulsar_of = {k: b.pulsar_of[int(i)] for k, i in enumerate(ids) if int(i) in b.pulsar_of}
+    src = np.array([b.trial_id(int(i)) for i in ids], np.int64)
+    return Batch(lengths, pack_offsets(lengths), pulsar_of, b.seed, src)
 
 
 def pack_offsets(lengths, align: int = 32) -> np.ndarray:
@@ -159,7 +173,7 @@ def uneven_batch(count: int = 2048, seed: int = SEED_BASE + 3,
 def batch_trial(b: Batch, i: int) -> np.ndarray:
     """Host copy of trial ``i`` of a batch (noise seeded per trial, plus its pulsar if any)."""
     p = [b.pulsar_of[i]] if i in b.pulsar_of else []
-    return spectrum(int(b.lengths[i]), b.seed * 4099 + i, p)
+    return spectrum(int(b.lengths[i]), b.seed * 4099 + b.trial_id(i), p)
 
 
 def batch_host(b: Batch) -> np.ndarray:
@@ -213,7 +227,7 @@ def device_batch(b: Batch, device, dtype=None):
     out = torch.zeros(b.total, dtype=torch.float32, device=device)
     for i in range(b.lengths.shape[0]):
         view = out[int(b.offsets[i]):int(b.offsets[i]) + int(b.lengths[i])]
-        device_noise(view.shape[0], b.seed * 4099 + i, device, out=view)
+        device_noise(view.shape[0], b.seed * 4099 + b.trial_id(i), device, out=view)
         if i in b.pulsar_of:
             device_inject(view, [b.pulsar_of[i]])
     return out if dtype is None else out.to(dtype)

@@ -1,6 +1,7 @@
 """The N > 1 host path on CPU: two gloo ranks shard an uneven batch longest-first, run the
 forward of their spectra, gather the per-spectrum results in global order and all-reduce the
-training step's dL/dw.  The per-rank compute is the FP64 oracle (the CPU stand-in for the GPU
+training step's dL/dw, through the same helpers (``shard_for_rank``, ``batch_step``,
+``grad_step``) that bench.py runs under torchrun.  The per-rank compute is the FP64 oracle (the CPU stand-in for the GPU
 forward / adjoint, which these ranks cannot run); what is tested is the sharding and the
 exchanges, against a single-process run of the whole batch."""
 import os
@@ -53,11 +54,22 @@ def _worker(rank, world, port, out_dir):
     b, xs = _batch()
     H = 8
     w = np.ones(1024)
-    shards = hsd.lpt_shards(b.lengths, world)
-    mine = shards[rank]
-    keys, gw = _rank_work(oracle, xs, mine, H, w)
-    all_keys = hsd.gather_by_spectrum(torch.from_numpy(keys), mine, len(xs))
-    gw_t = hsd.allreduce_sum(torch.from_numpy(gw))
+    # the helpers bench.py runs under torchrun, with the oracle as each rank's compute
+    mine = hsd.shard_for_rank(b.lengths, world, rank)
+    # each rank draws only its own trials, packed as synth.sub_batch lays them out (as on a GPU)
+    sb = synth.sub_batch(b, mine)
+    xs_local = [synth.batch_trial(sb, k) for k in range(len(mine))]
+    assert all(np.array_equal(a, xs[i]) for a, i in zip(xs_local, mine))
+    local_ids = list(range(len(mine)))
+
+    def forward(idx):
+        assert list(idx) == list(mine)
+        return torch.from_numpy(_rank_work(oracle, xs_local, local_ids, H, w)[0])
+
+    all_keys = hsd.batch_step(mine, len(xs), forward)
+    gw_t = hsd.grad_step(lambda: torch.from_numpy(_rank_work(oracle, xs_local, local_ids, H, w)[1]))
+    local = hsd.batch_step(mine, len(xs), forward, gather=False)
+    assert local.shape[0] == len(mine)
     tmax = hsd.max_over_ranks(float(rank + 1))
     np.savez(os.path.join(out_dir, f"rank{rank}.npz"), keys=all_keys.numpy(), gw=gw_t.numpy(), tmax=tmax,
              shard=np.array(mine))

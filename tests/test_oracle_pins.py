@@ -650,3 +650,36 @@ def test_golden_footprints_match_oracle(oracle_lib):
     path = oracle_lib.greedy_1d(x, 32, *unit_norm(32))[2]
     assert gold["long"]["fused"]["sectors"] == oracle_lib.sectors_1d(3, 4, x.size, 32, path=path)
     assert gold["long"]["simple"]["sectors"] == oracle_lib.sectors_1d(1, 4, x.size, 32)
+
+
+def test_openmp_build_matches_the_oracle(oracle_lib, tmp_path):
+    """The all-core CPU baseline (liboracle_omp.so, the same source with its loops over
+    fundamentals split over OpenMP threads) returns what the single-threaded oracle returns."""
+    import subprocess
+    import sys
+    o = oracle_lib
+    if not os.path.exists(o.LIB_OMP):
+        pytest.skip("no OpenMP in this compiler")
+    x = synth.spectrum(40000, 12, [synth.Pulsar(123.4, 0.05)])
+    pl = synth.plane(2048, 41, 20, 8)
+    np.save(tmp_path / "x.npy", x)
+    np.save(tmp_path / "pl.npy", pl)
+    code = (
+        "import os, sys, numpy as np\n"
+        "os.environ['OMP_NUM_THREADS'] = '4'\n"
+        "import oracle\n"
+        "assert oracle.use_openmp()\n"
+        "x = np.load(sys.argv[1] + '/x.npy'); pl = np.load(sys.argv[1] + '/pl.npy')\n"
+        "z, one = np.zeros(32), np.ones(32)\n"
+        "s = oracle.simple_1d(x, 32, z, one, want_all=True)\n"
+        "g = oracle.greedy_1d(x, 32, z, one, want_all=True)\n"
+        "q = oracle.greedy_2d(pl, 20, 3, z[:3], one[:3], want_all=True)\n"
+        "np.savez(sys.argv[1] + '/out.npz', *s, *g, *q)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.check_call([sys.executable, "-c", code, str(tmp_path)], cwd=root)
+    got = np.load(tmp_path / "out.npz")
+    z, one = np.zeros(32), np.ones(32)
+    want = [*o.simple_1d(x, 32, z, one, want_all=True), *o.greedy_1d(x, 32, z, one, want_all=True),
+            *o.greedy_2d(pl, 20, 3, z[:3], one[:3], want_all=True)]
+    for i, w in enumerate(want):
+        assert np.array_equal(got[f"arr_{i}"], w), i
