@@ -82,6 +82,16 @@ __device__ __forceinline__ void set_error(int *err, int code)
 // first.  Returns at once when the kernel was launched without the attribute or the reset is done.
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// atomicMax of a per-spectrum argmax key, skipped when the key already stored is at least as
+// large: keys only grow during a pass, so a smaller or equal key can never win, and on a spectrum
+// of thousands of CTAs only the few that raise the running maximum reach the L2 atomic unit (the
+// others would serialise there on one address).  Called after wait_prior_grid().
+__device__ __forceinline__ void argmax_update(unsigned long long *dst, unsigned long long key)
+{
+    const unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(dst);
+    if (key > cur) atomicMax(dst, key);
+}
+
 // Block-wide max of a 64-bit key, then one atomicMax per CTA.
 __device__ __forceinline__ void block_argmax(unsigned long long key, unsigned long long *dst,
                                              unsigned long long *scratch /*[32] smem*/)
@@ -102,7 +112,7 @@ __device__ __forceinline__ void block_argmax(unsigned long long key, unsigned lo
         }
         if (lane == 0 && key != 0ull) {
             wait_prior_grid();
-            atomicMax(dst, key);
+            argmax_update(dst, key);
         }
     }
 }

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256, (HC == 8 || HC == 32) ? 5 : 4) k_fwd1d_op
     for (; i < iend; ++i) {
         if (i >= fe) {
             // next spectrum: flush the argmax of the previous one, locate the new one
-            if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) atomicMax(o.argmax + s, kmax);
+            if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) argmax_update(o.argmax + s, kmax);
             kmax = 0ull;
             int lo = 0, hi = a.B - 1;
             while (lo < hi) {
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256, (HC == 8 || HC == 32) ? 5 : 4) k_fwd1d_op
             kmax = key > kmax ? key : kmax;
         }
     }
-    if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) atomicMax(o.argmax + s, kmax);
+    if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) argmax_update(o.argmax + s, kmax);
 }
 
 // H = 32 without the truncated tail: two consecutive fundamentals A = n and B = n + 1 of one
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd1d_opt_pair(const Fwd1DArgs a, co
     const int lkP = hl + 1 - dmax1;       // phase 1: the same for drift hl
     while (i < iend) {
         if (i >= fe) {
-            if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) atomicMax(o.argmax + s, kmax);
+            if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) argmax_update(o.argmax + s, kmax);
             kmax = 0ull;
             int lo = 0, hi = a.B - 1;
             while (lo < hi) {
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd1d_opt_pair(const Fwd1DArgs a, co
         __syncwarp();   // the next pair's B states may overwrite the slots
         i += pairB ? 2 : 1;
     }
-    if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) atomicMax(o.argmax + s, kmax);
+    if (s >= 0 && o.argmax && lane == 0 && kmax != 0ull) argmax_update(o.argmax + s, kmax);
 }
 
 template <typename T, bool WHITEN>

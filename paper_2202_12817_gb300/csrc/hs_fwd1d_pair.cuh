@@ -15,6 +15,12 @@
 
 namespace hs {
 
+// A load the compiler may not merge with an earlier load of the same address.
+__device__ __forceinline__ int64_t ld_volatile_i64(const int64_t *p)
+{
+    return *reinterpret_cast<const volatile int64_t *>(p);
+}
+
 // CH: fundamentals (chains) per lane, interleaved order by order so that each lane keeps CH
 // loads in flight; a tile is CH x (fundamentals per CTA pass).  32 registers a thread at most,
 // so every thread slot of an SM is usable.
@@ -66,16 +72,17 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
             for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) {
                 const int f = i / H, h = i - f * H;
-                const FormArgs &fa = f ? a.g : a.s;
+                // select the pointers, not the parameter struct (indexing it would copy it to local memory)
+                const float *sg = f ? a.g.sigma : a.s.sigma;
+                const float *mu = f ? a.g.mu : a.s.mu;
                 if ((FORMS >> f) & 1) {
-                    const float rs = __frcp_rn(__ldg(fa.sigma + no + h));
-                    tab[h][f] = make_float2(rs, __fmul_rn(__ldg(fa.mu + no + h), rs));
+                    const float rs = __frcp_rn(__ldg(sg + no + h));
+                    tab[h][f] = make_float2(rs, __fmul_rn(__ldg(mu + no + h), rs));
                 }
             }
             __syncthreads();
             loaded_spec = s;
         }
-        const int64_t fbase = __ldg(a.fund_off + s);
         const int64_t nf = __ldg(a.nf_main + s);
         const int64_t n0 = (tile - __ldg(a.tile_start + s)) * (CH * fpp) + li;
         const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
@@ -132,11 +139,16 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
             }
         }
         unsigned long long key = 0ull;
+        // the tile's offsets are read again rather than kept live through the order loop (the
+        // loop then fits the 32 registers a thread has at full occupancy without spilling)
+        const int64_t nf2 = ld_volatile_i64(a.nf_main + s);
+        const int64_t n02 = (tile - ld_volatile_i64(a.tile_start + s)) * (CH * fpp) + li;
+        const int64_t fbase2 = ld_volatile_i64(a.fund_off + s);
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-            const int64_t n = n0 + static_cast<int64_t>(c) * fpp;
-            if (n < nf) {
-                const int64_t o = fbase + n;
+            const int64_t n = n02 + static_cast<int64_t>(c) * fpp;
+            if (n < nf2) {
+                const int64_t o = fbase2 + n;
                 (greedy ? a.g.snr : a.s.snr)[o] = rm[c].best;
                 (greedy ? a.g.best_h : a.s.best_h)[o] = static_cast<uint8_t>(rm[c].bh);
                 if (greedy && a.g.path) store_path(a.g.path, a.path_bytes, o, bits[c]);
@@ -161,7 +173,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
                         mx = red[threadIdx.x][i] > mx ? red[threadIdx.x][i] : mx;
                     if (mx != 0ull) {
                         wait_prior_grid();
-                        atomicMax(dst + s, mx);
+                        argmax_update(dst + s, mx);
                     }
                 }
             }

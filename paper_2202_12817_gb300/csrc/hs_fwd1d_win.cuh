@@ -130,7 +130,7 @@ __device__ __forceinline__ void consumer_argmax(unsigned long long key, unsigned
         }
         if (lane == 0 && key != 0ull) {
             wait_prior_grid();
-            atomicMax(dst, key);
+            argmax_update(dst, key);
         }
     }
     consumer_sync(nthreads);
