@@ -144,7 +144,7 @@ struct SweepGeom {
 // Geometry of the sweep with band width Wb and `threads` per CTA; ok = false where the sweep
 // does not apply (checked plans, a row stride that is not a multiple of 16 bytes, more staged
 // rows than one tensor-copy box holds, tiles beyond shared memory, nothing beyond the prefix).
-SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2)
+SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t prefix_bands = kSweepPrefixBands)
 {
     SweepGeom g;
     const hs_desc &d = p->d;
@@ -171,7 +171,7 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2)
     for (int64_t h = 2; h <= H; ++h) state_cap += (Wb + h - 1) / h * nz * 16;
     const int64_t buf = (tile + state_cap + 127) / 128 * 128;
     if (nbuf < 2 || nbuf > kSweepMaxStages || nbuf * buf + kSweepStaticSmem > kSweepSmemLimit) return g;
-    const int64_t f_s = std::max<int64_t>(p->f_lo, kSweepPrefixBands * Wb);
+    const int64_t f_s = std::max<int64_t>(p->f_lo, prefix_bands * Wb);
     if (f_s > p->f_hi) return g;
     const int compute = threads - 64;   // warps 0 and 1 control and publish
     if (compute < 32) return g;
@@ -385,10 +385,11 @@ hs_tuning default_tuning(const hs_plan p)
         (p->d.forms & 3) == 3 && !(p->d.flags & HS_FLAG_WHITENING))
         return hs_tuning{3, 128, 2, 0, 0, 0, 0, (p->d.dtype != HS_F32 && p->d.num_spectra > 1) ? 2 : 0, 0};
     // Measured on the 2^23-bin H = 32 spectrum (GB300): FP32 without whitening runs fastest on
-    // the paired-lane kernel 6 (fused 43 us vs 45 us, simple 25.6 vs 27.8 us, greedy equal);
-    // with whitening or 16-bit storage the direct kernel 0 is as fast or faster (256-thread CTAs
-    // for FP32, 128 for 16-bit storage).  HS_FLAG_AUTOTUNE times the alternatives per plan.
-    if (p->d.dtype == HS_F32 && !(p->d.flags & HS_FLAG_WHITENING)) return hs_tuning{6, 256, 1, 0, 0, 0, 0, 0, 0};
+    // the paired-lane kernel 6 in 128-thread CTAs (fused 42.9 us vs 43.6 us with 256 threads and
+    // 45.3 us on kernel 0; an L2 prefetch of the whole input first costs 2.5 us); with whitening or
+    // 16-bit storage the direct kernel 0 is as fast or faster (kernel 6 on FP16: 33.3 vs 32.8 us).
+    // HS_FLAG_AUTOTUNE times the alternatives per plan.
+    if (p->d.dtype == HS_F32 && !(p->d.flags & HS_FLAG_WHITENING)) return hs_tuning{6, 128, 1, 0, 0, 0, 0, 0, 0};
     return hs_tuning{0, p->d.dtype == HS_F32 ? 256 : 128, 1, 0, 0, 0, 0, 0, 0};
 }
 
@@ -638,6 +639,9 @@ int sweep_wb(const hs_plan p)
     return p->tun.stage_kb > 0 ? 16 * p->tun.stage_kb : sweep_default_wb(p->d.dtype);
 }
 int sweep_stages(const hs_plan p) { return p->tun.stages > 0 ? p->tun.stages : 2; }
+// Chains f < prefix bands x Wb run whole in registers (prefix tasks); tuning.producers scales the
+// default 64 bands (0 or 1: 64, k: 64 k).
+int64_t sweep_prefix(const hs_plan p) { return kSweepPrefixBands * std::max(1, p->tun.producers); }
 
 // Enqueue the forward pass (memsets + the main kernel + the truncated tail's) on `st`.
 // chunk >= 0 (1D): only the tiles of that chunk of the pipelined host input, on the tile prefix
@@ -663,7 +667,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         a.g = to_form_args(greedy);
         a.err = p->d_err;
         if (p->tun.kernel == 2 && ws) {
-            const SweepGeom g = sweep_geom(p, sweep_wb(p), p->tun.threads, sweep_stages(p));
+            const SweepGeom g = sweep_geom(p, sweep_wb(p), p->tun.threads, sweep_stages(p), sweep_prefix(p));
             if (g.ok) return launch_sweep(p, a, g, ws, st);
         }
         // kernel 2 without a workspace runs as kernel 1 (the outputs are the same bit for bit)
@@ -1303,16 +1307,17 @@ hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
         // 2D: kernel 0 = f-tiles fastest, 1 = z rows fastest (256 threads, nothing else);
         // kernel 2 = the column sweep (256 or 512 threads, stage_kb = band width / 16, ctas_per_sm)
         if (!t || t->kernel < 0 || t->kernel > 2 || t->fund_per_thread != 1 || t->dynamic || t->prefetch ||
-            t->producers)
+            t->producers < 0 || t->producers > 64)
             return HS_ERR_INVALID_ARG;
-        if (t->kernel < 2 && (t->threads != 256 || t->ctas_per_sm || t->stage_kb || t->stages))
+        if (t->kernel < 2 && (t->threads != 256 || t->ctas_per_sm || t->stage_kb || t->stages || t->producers))
             return HS_ERR_INVALID_ARG;
         if (t->kernel == 2) {
             if ((t->threads != 256 && t->threads != 512 && t->threads != 1024) || t->ctas_per_sm < 0 || t->ctas_per_sm > 4 ||
                 t->stage_kb < 0 || t->stages < 0 || t->stages == 1 || t->stages > kSweepMaxStages)
                 return HS_ERR_INVALID_ARG;
             const int wb = t->stage_kb > 0 ? 16 * t->stage_kb : sweep_default_wb(p->d.dtype);
-            const SweepGeom g = sweep_geom(p, wb, t->threads, t->stages > 0 ? t->stages : 2);
+            const SweepGeom g = sweep_geom(p, wb, t->threads, t->stages > 0 ? t->stages : 2,
+                                           kSweepPrefixBands * std::max(1, t->producers));
             if (!g.ok || g.state_bytes + g.sync_bytes > fwd_workspace_bytes(p)) return HS_ERR_UNSUPPORTED;
         }
         std::lock_guard<std::mutex> lk(p->mu);

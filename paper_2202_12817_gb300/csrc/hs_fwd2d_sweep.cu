@@ -127,7 +127,9 @@ struct BandHdr {
     long long fa[kMaxH2D];     // order h = k + 1 holds chains [fa[k], fa[k] + nf[k]), all z
     int nf[kMaxH2D];
     int soff[kMaxH2D];         // int4 offset of order h's state segment in the buffer
-    float inv[kMaxH2D];        // 1 / nf (row split of the event index)
+    int ev[kMaxH2D + 1];       // events of orders < h: order h's events are [ev[h-1], ev[h])
+    unsigned long long mg[kMaxH2D];  // floor(2^32 / nf) + 1: i / nf = (i mg) >> 32 for the event
+                                     // index i of an order (i nf < 2^32)
 };
 }  // namespace
 
@@ -264,15 +266,24 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 if (t >= total) break;
             } else {
                 const int cnt = static_cast<int>(p_nf) * nz, scnt = lane > 0 ? cnt : 0;
+                // inclusive prefix over the orders of their event counts
+                int einc = lane < H ? cnt : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int w = __shfl_up_sync(0xffffffffu, einc, o);
+                    if (lane >= o) einc += w;
+                }
                 if (lane < H) {
                     hdr[b].fa[lane] = p_fa;
                     hdr[b].nf[lane] = static_cast<int>(p_nf);
-                    hdr[b].inv[lane] = p_nf > 0 ? __frcp_rn(static_cast<float>(p_nf)) : 0.f;
+                    hdr[b].mg[lane] = p_nf > 0 ? (0x100000000ull / p_nf) + 1ull : 0ull;
                     hdr[b].soff[lane] = p_sinc - scnt;
+                    hdr[b].ev[lane + 1] = einc;
                 }
                 if (lane == 0) {
                     hdr[b].task = t;
                     hdr[b].c0 = p_c0;
+                    hdr[b].ev[0] = 0;
                 }
                 // dependencies: poll (bounded) the flags that were still clear when prepared; the
                 // bulk copies then read through the async proxy what other CTAs stored through the
@@ -394,40 +405,54 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
             const T *tile = reinterpret_cast<const T *>(buf);
             const int4 *sst = reinterpret_cast<const int4 *>(buf + s.tile_bytes);
             const int col0 = static_cast<int>(hd.c0 - kSweepHalo);   // plane column of tile column 0
-            // the band's events order by order (the per-order values are uniform across threads)
-            for (int h = 1; h <= H; ++h) {
-                const int nf = hd.nf[h - 1];
-                if (nf == 0) continue;
-                const int n = nf * nz, fa = static_cast<int>(hd.fa[h - 1]), so = hd.soff[h - 1];
-                const float inv = hd.inv[h - 1], rsh = rs[h - 1], mursh = murs[h - 1];
-                const int zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
-                for (int i = ctid; i < n; i += NC) {
-                    int zi = __float2int_rz((static_cast<float>(i) + 0.5f) * inv);
-                    if (zi * nf > i) --zi;
-                    else if ((zi + 1) * nf <= i) ++zi;
-                    const int fi = i - zi * nf;
-                    const int f = fa + fi;
-                    Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
-                    if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
-                    const int cf = h * f + ch.df;
-                    const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
-                    const T *p0 = tile + cr * P + (cf - 1 - col0);
-                    float v9[9];
+            // the band's events of every order as one index space e in [0, ev[H]): order h holds
+            // [ev[h-1], ev[h]), within it event i is chain (fa + i % nf, z_lo + i / nf).  Every
+            // event of a band is independent of the others (order h of chain f anchors at h f, order
+            // h + 1 at h f + f >= h f + Wb: a later band), so the orders need no barrier between them
+            // and no thread idles while the high orders, which hold few events, run.  A thread's
+            // events increase, so its order h only moves up.
+            const int E = hd.ev[H];
+            int h = 0, e_hi = 0, nf = 0, fa = 0, so = 0, zrow = 0;
+            unsigned long long mg = 0ull;
+            float rsh = 0.f, mursh = 0.f;
+            for (int e = ctid; e < E; e += NC) {
+                if (e >= e_hi) {
+                    do {
+                        ++h;
+                        e_hi = hd.ev[h];
+                    } while (e >= e_hi);
+                    nf = hd.nf[h - 1];
+                    fa = static_cast<int>(hd.fa[h - 1]);
+                    so = hd.soff[h - 1];
+                    mg = hd.mg[h - 1];
+                    rsh = rs[h - 1];
+                    mursh = murs[h - 1];
+                    zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
+                }
+                const unsigned i = static_cast<unsigned>(e - hd.ev[h - 1]);
+                const int zi = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
+                const int fi = static_cast<int>(i) - zi * nf;
+                const int f = fa + fi;
+                Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
+                if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
+                const int cf = h * f + ch.df;
+                const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
+                const T *p0 = tile + cr * P + (cf - 1 - col0);
+                float v9[9];
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
+                for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
-                    chain2d_step(ch, h, v9, rsh, mursh);
-                    if (h == H) {
-                        const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
-                        a.g.snr[o] = ch.best;
-                        a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
-                        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
-                        const unsigned long long kx = argmax_key(ch.best, o);
-                        key = kx > key ? kx : key;
-                    } else {
-                        st_state(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
-                    }
+                    for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
+                chain2d_step(ch, h, v9, rsh, mursh);
+                if (h == H) {
+                    const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
+                    a.g.snr[o] = ch.best;
+                    a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
+                    if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
+                    const unsigned long long kx = argmax_key(ch.best, o);
+                    key = kx > key ? kx : key;
+                } else {
+                    st_state(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
                 }
             }
             // every compute thread is done with the buffer and has issued its stores: release the

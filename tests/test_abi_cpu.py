@@ -154,7 +154,7 @@ def test_tuning_validation(hs):
     p = plan(hs, H=8, forms=3, lengths=[10000])
     t = p.tuning
     assert t.threads in (64, 128, 256) and t.fund_per_thread == 1
-    assert t.kernel == 6 and t.threads == 256          # FP32: paired lanes
+    assert t.kernel == 6 and t.threads == 128          # FP32: paired lanes
     t16 = plan(hs, H=8, forms=3, lengths=[10000], dtype=hs.F16).tuning
     assert t16.kernel == 0 and t16.threads == 128
     p.tuning = dict(kernel=0, threads=128, fund_per_thread=1, ctas_per_sm=4, dynamic=1)

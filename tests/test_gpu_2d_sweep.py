@@ -23,6 +23,15 @@ def test_sweep_band_widths(hs, oracle_lib, stage_kb, threads):
     run_2d(hs, oracle_lib, pl, z0, 8, tuning=dict(kernel=2, threads=threads, stage_kb=stage_kb))
 
 
+@pytest.mark.parametrize("producers", [2, 5])
+def test_sweep_longer_prefix(hs, oracle_lib, producers):
+    """tuning.producers moves the start of the sweep to f = 64 producers Wb: more chains run whole
+    in registers, the sweep's first band starts later; the outputs do not change."""
+    z0 = 30
+    pl = synth.plane(120000, 2 * z0 + 1, z0, 170 + producers, synth.random_tracks(4, 120000, 23, f_lo=50, zmax=3))
+    run_2d(hs, oracle_lib, pl, z0, 8, tuning=dict(kernel=2, threads=512, stage_kb=1, producers=producers))
+
+
 @pytest.mark.parametrize("H", [1, 2, 3, 5, 8])
 def test_sweep_orders(hs, oracle_lib, H):
     z0 = 24
@@ -88,7 +97,8 @@ def test_sweep_equals_kernel1(hs, dtype):
         pl = pl.half()
     pl_dev = pl.to(DEV)
     outs = []
-    for t in (dict(kernel=1, threads=256), dict(kernel=2, threads=512), dict(kernel=2, threads=256, stage_kb=2)):
+    for t in (dict(kernel=1, threads=256), dict(kernel=2, threads=512), dict(kernel=2, threads=256, stage_kb=2),
+              dict(kernel=2, threads=1024, producers=4)):
         plan = hs.Plan(8, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=201, z0_row=100, dtype=dtype)
         plan.tuning = t
         outs.append(_outputs(hs, plan, pl_dev, 8))
