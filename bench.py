@@ -186,11 +186,19 @@ def oracle_rate_1d(x_host, H, budget_s=8.0, frac=1.0, forms=3):
     return reps * nf * H / el, f"{reps} x fundamentals [0, {nf}) of a {x_host.size}-bin spectrum, {what}, 1 thread"
 
 
-def oracle_rate_2d(plane_host, z0_row, H, budget_s=8.0, z_rows=1):
+def plane_sample(plane_host, H, f_count=16384):
+    """The columns of the plane that the fundamentals f < f_lo + f_count read (every z): a
+    bounded CPU-baseline sample of the 2D workload."""
+    ncols = min(plane_host.shape[1], H * (1 + f_count) + H + 1)
+    return np.ascontiguousarray(plane_host[:, :ncols])
+
+
+def oracle_rate_2d(plane_host, z0_row, H, budget_s=8.0):
+    """Time the single-thread oracle over every fundamental of `plane_host` (a column slice)."""
     import oracle
     oracle.build()
     f_lo, f_hi, z_lo, z_hi = oracle.domain_2d(plane_host.shape[1], plane_host.shape[0], z0_row, H)
-    dom = (f_lo, f_hi, 0, z_rows - 1)
+    dom = (f_lo, f_hi, z_lo, z_hi)
     mu, sg = oracle.norm_exponential(2, 2, H, mean1=2.0)
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -199,8 +207,9 @@ def oracle_rate_2d(plane_host, z0_row, H, budget_s=8.0, z_rows=1):
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    units = reps * (f_hi - f_lo + 1) * z_rows * H
-    return units / el, f"{reps} x z in [0, {z_rows}) x all {f_hi - f_lo + 1} f of the plane, 1 thread"
+    units = reps * (f_hi - f_lo + 1) * (z_hi - z_lo + 1) * H
+    return units / el, (f"{reps} x every (f, z) fundamental of a {plane_host.shape[0]} x {plane_host.shape[1]} "
+                        "plane, 1 thread")
 
 
 def host_cores() -> int:
@@ -223,7 +232,7 @@ def oracle_rate_all_cores(spec, budget_s):
         if spec["dims"] == 1:
             cmd += ["--forms", str(spec.get("forms", 3)), "--frac", str(spec.get("frac", 1.0))]
         else:
-            cmd += ["--z0", str(spec["z0"]), "--zrows", str(spec.get("zrows_all", 16))]
+            cmd += ["--z0", str(spec["z0"])]
         try:
             r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=120 + 4 * budget_s)
             return json.loads(r.stdout.strip().splitlines()[-1])
@@ -239,7 +248,7 @@ def cpu_baseline(spec, budget_one, budget_all):
         v1, s1 = oracle_rate_1d(spec["x"], spec["H"], budget_s=budget_one, frac=spec.get("frac", 1.0),
                                 forms=spec.get("forms", 3))
     else:
-        v1, s1 = oracle_rate_2d(spec["x"], spec["z0"], spec["H"], budget_s=budget_one, z_rows=1)
+        v1, s1 = oracle_rate_2d(spec["x"], spec["z0"], spec["H"], budget_s=budget_one)
     one = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": s1}
     allc = oracle_rate_all_cores(spec, budget_all)
     if not allc or allc.get("threads", 1) <= 1:
@@ -630,8 +639,8 @@ def wl_plane(args, hs, torch, dev, world, dist):
         "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }
-    return result, clk.summary(), {"dims": 2, "x": pl.float().cpu().numpy(), "H": H, "z0": synth.PLANE_Z0_ROW,
-                                   "zrows_all": 16}
+    return result, clk.summary(), {"dims": 2, "x": plane_sample(pl.float().cpu().numpy(), H), "H": H,
+                                   "z0": synth.PLANE_Z0_ROW}
 
 
 def wl_grad(args, hs, torch, dev, world, dist):

@@ -4,12 +4,13 @@ Run by ``bench.py`` in a subprocess, so that the OpenMP runtime of the all-core 
 shares a process with torch's:
 
     python -m oracle.timing --input x.npy --H 32 --forms 3 --threads T --budget S [--frac F]
-    python -m oracle.timing --input plane.npy --dims 2 --z0 100 --H 8 --zrows K --threads T --budget S
+    python -m oracle.timing --input plane.npy --dims 2 --z0 100 --H 8 --threads T --budget S
 
 threads = 1 times liboracle.so (the oracle proper, one thread); threads > 1 times
 liboracle_omp.so, the same source with its loops over fundamentals spread over `threads`
 OpenMP threads.  The oracle runs repeatedly over a bounded sample of the input (the first
-`frac` of a spectrum's fundamentals, or the first `zrows` rows of fdot fundamentals of a plane)
+`frac` of a spectrum's fundamentals, or every fundamental of a plane: the caller passes a slice
+of the columns of a larger plane)
 until `budget` seconds have passed.  Prints one JSON line: units (bins x harmonics) per second,
 the threads used, the sample and the host CPU model.
 """
@@ -51,7 +52,6 @@ def main(argv=None):
     ap.add_argument("--budget", type=float, default=5.0)
     ap.add_argument("--frac", type=float, default=1.0)
     ap.add_argument("--z0", type=int, default=0)
-    ap.add_argument("--zrows", type=int, default=1)
     a = ap.parse_args(argv)
     if a.threads > 1:
         os.environ["OMP_NUM_THREADS"] = str(a.threads)
@@ -80,7 +80,7 @@ def main(argv=None):
         sample = f"{reps} x fundamentals [0, {nf}) of a {x.size}-bin spectrum, {what}"
     else:
         f_lo, f_hi, z_lo, z_hi = oracle.domain_2d(x.shape[1], x.shape[0], a.z0, H)
-        dom = (f_lo, f_hi, 0, a.zrows - 1)
+        dom = (f_lo, f_hi, z_lo, z_hi)
         mu, sg = oracle.norm_exponential(2, 2, H, mean1=2.0)
         while True:
             oracle.greedy_2d(x, a.z0, H, mu, sg, dom=dom)
@@ -88,8 +88,8 @@ def main(argv=None):
             el = time.perf_counter() - t0
             if el >= a.budget:
                 break
-        units = reps * (f_hi - f_lo + 1) * a.zrows * H
-        sample = f"{reps} x z in [0, {a.zrows}) x all {f_hi - f_lo + 1} f of the plane"
+        units = reps * (f_hi - f_lo + 1) * (z_hi - z_lo + 1) * H
+        sample = f"{reps} x every (f, z) fundamental of a {x.shape[0]} x {x.shape[1]} plane"
     print(json.dumps({"rate": units / el, "threads": threads, "sample": sample + f", {threads} thread(s)",
                       "cpu": cpu_model(), "seconds": el}))
 
