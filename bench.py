@@ -65,10 +65,11 @@ KERNEL_SOURCES = {
     "longbf16": ["hs_fwd1d.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_bf16.cu", "hs_internal.cuh"],
     "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
     "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
-    "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
-    "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
-    "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh"],
-    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "table2": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
 }
 
 
@@ -751,8 +752,10 @@ def wl_table2(args, hs, torch, dev, world, dist):
     out = {}
     clk_all = None
     for name, flags in (("main", 0), ("all_bins", hs.FLAG_TRUNCATE_TAIL)):
-        plan = hs.Plan(H, hs.GREEDY, lengths=b.lengths, offsets=b.offsets[:-1], flags=flags | hs.FLAG_AUTOTUNE,
-                       device=dev.index)
+        plan = hs.Plan(H, hs.GREEDY, lengths=b.lengths, offsets=b.offsets[:-1],
+                       flags=flags | (0 if args.tuning else hs.FLAG_AUTOTUNE), device=dev.index)
+        if args.tuning:
+            plan.tuning = json.loads(args.tuning)
         io = plan.alloc_form(mu, sg, path=True, argmax=True)
         ws = None if not plan.workspace_bytes else plan.workspace(dev)
 
