@@ -723,9 +723,9 @@ def wl_grad(args, hs, torch, dev, world, dist):
         "roofline": roofline(fwd_bytes + bwd_bytes, ms, peak, peak_kind, "grad",
                              "fwd: oracle sector fraction x input + w + outputs; bwd: input + forward outputs + dL/dw",
                              plan.tuning.as_dict()),
-        # per step: the forward pass, the adjoint's marking pass, the adjoint and (spectra summed in
-        # more than one group) the reduction of the partial dL/dw
-        "gpu_launches": (3 + (1 if B > 1 else 0)) * steps, "wall_s_timed_region": round(wall, 3),
+        # per step: the whitened copy, the forward pass, the adjoint's marking pass, the adjoint and
+        # (spectra summed in more than one group) the reduction of the partial dL/dw
+        "gpu_launches": (4 + (1 if B > 1 else 0)) * steps, "wall_s_timed_region": round(wall, 3),
     }
     return result, clk.summary(), {"dims": 1, "x": p[:N].detach().cpu().numpy(), "H": H, "forms": 2}
 

@@ -156,7 +156,11 @@ hs_status hs_plan_input_offsets(hs_plan plan, int64_t *offsets);
 /* 2D fundamental domain: f in [f_lo, f_hi], z in [z_lo, z_hi]. */
 hs_status hs_plan_domain_2d(hs_plan plan, int64_t *f_lo, int64_t *f_hi, int64_t *z_lo, int64_t *z_hi);
 /* Bytes of device workspace hs_run / hs_backward take (0 = pass NULL): the forward's dynamic
- * schedule needs 256 bytes; a 2D plane that admits the column sweep (kernel 2 below) adds 16
+ * schedule needs 256 bytes; a 1D plan with HS_FLAG_WHITENING adds 4 bytes per input element (hs_run
+ * given a workspace first writes the whitened input fl32(w[j] p[j]) there, then runs the pass on
+ * that FP32 copy -- the same outputs bit for bit, one gather per loaded value instead of two;
+ * without a workspace, and in hs_run_host and hs_run_fixed_scratch, the pass multiplies as it
+ * loads); a 2D plane that admits the column sweep (kernel 2 below) adds 16
  * bytes of chain state per fundamental it sweeps and 4 bytes per band; the adjoint uses one
  * partial dL/dw (N floats) per group of spectra (up to 16 groups; required for a whitening plan
  * with grad_w) followed by one byte per (spectrum, 1024-bin block) that marks the blocks

@@ -195,9 +195,18 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t
 // Forward workspace: the dynamic schedule's tile counter (1D); the sweep's chain state and band
 // flags (2D), sized for the narrowest band (16 columns: the most bands; any band width the sweep
 // can take, 16 can take too).
+// 1D with whitening: the forward writes the whitened input fl32(w[j] p[j]) (FP32, at the input's
+// offsets) into the workspace after the tile counter, then runs the plain pass on it.
+constexpr size_t kWhitenedOffset = kWorkspaceBytes;
+size_t whitened_bytes(const hs_plan p)
+{
+    if (p->d.dims != 1 || !(p->d.flags & HS_FLAG_WHITENING)) return 0;
+    return (static_cast<size_t>(p->extent) * 4 + 255) / 256 * 256;
+}
+
 size_t fwd_workspace_bytes(const hs_plan p)
 {
-    if (p->d.dims == 1) return kWorkspaceBytes;
+    if (p->d.dims == 1) return kWorkspaceBytes + whitened_bytes(p);
     const SweepGeom n = sweep_geom(p, 16, kSweepThreads);   // the most bands and the most sweep chains
     return n.ok ? n.state_bytes + n.sync_bytes : 0;
 }
@@ -493,6 +502,20 @@ const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
     return nullptr;
 }
 
+// A stored 16-bit value widened exactly to FP32.
+template <typename T>
+__device__ __forceinline__ float widen16(unsigned int bits);
+template <>
+__device__ __forceinline__ float widen16<__half>(unsigned int bits)
+{
+    return __half2float(__ushort_as_half(static_cast<unsigned short>(bits)));
+}
+template <>
+__device__ __forceinline__ float widen16<__nv_bfloat16>(unsigned int bits)
+{
+    return __uint_as_float(bits << 16);
+}
+
 // Clears the per-spectrum argmax keys of both forms and the dynamic schedule's tile counter before
 // a 1D pass.  Its first instruction lets the pass that follows it on the stream start at once
 // (programmatic dependent launch); the pass waits for this kernel only before its first argmax
@@ -507,6 +530,53 @@ __global__ void k_fwd_reset(unsigned long long *s_key, unsigned long long *g_key
         if (g_key) g_key[i] = 0ull;
     }
     if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
+}
+
+// Whitened copy of a whitening plan's input: X[o_s + j] = fl32(w[j] p_s[j]) for every spectrum s
+// (offset o_s) and bin j < N, the product each pass kernel would form as it loads (the same single
+// rounding, so the pass on X gives the same outputs bit for bit).  Four bins per thread where the
+// input is 16-byte aligned (offsets and w are; N may leave a ragged tail).  Also clears the argmax
+// keys and the tile counter, as k_fwd_reset does.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prewhiten(const T *p, const float *w, float *X, const int64_t *in_off,
+                                                   int32_t B, int64_t N, unsigned long long *s_key,
+                                                   unsigned long long *g_key, unsigned long long *counter)
+{
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < B; i += blockDim.x) {
+            if (s_key) s_key[i] = 0ull;
+            if (g_key) g_key[i] = 0ull;
+        }
+        if (counter && threadIdx.x == 0) *counter = 0ull;
+    }
+    const int64_t cps = (N + 1023) / 1024;   // 1024-bin chunks per spectrum
+    const int64_t total = cps * B;
+    for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+        const int64_t sp = c / cps;
+        const int64_t j0 = (c - sp * cps) * 1024 + 4 * threadIdx.x;
+        const int64_t o = __ldg(in_off + sp);
+        if (j0 + 3 < N) {
+            const float4 wv = __ldg(reinterpret_cast<const float4 *>(w + j0));
+            float v0, v1, v2, v3;
+            if constexpr (sizeof(T) == 4) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(p + o + j0));
+                v0 = q.x; v1 = q.y; v2 = q.z; v3 = q.w;
+            } else {
+                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + o + j0));
+                v0 = widen16<T>(q.x & 0xffffu); v1 = widen16<T>(q.x >> 16);
+                v2 = widen16<T>(q.y & 0xffffu); v3 = widen16<T>(q.y >> 16);
+            }
+            *reinterpret_cast<float4 *>(X + o + j0) =
+                make_float4(__fmul_rn(wv.x, v0), __fmul_rn(wv.y, v1), __fmul_rn(wv.z, v2), __fmul_rn(wv.w, v3));
+        } else {
+            for (int64_t j = j0; j < N && j < j0 + 4; ++j) {
+                float v;
+                if constexpr (sizeof(T) == 4) v = __ldg(reinterpret_cast<const float *>(p) + o + j);
+                else v = widen16<T>(__ldg(reinterpret_cast<const unsigned short *>(p) + o + j));
+                X[o + j] = __fmul_rn(__ldg(w + j), v);
+            }
+        }
+    }
 }
 
 // Launch of a 1D forward kernel; with `after_reset` it may start while k_fwd_reset (enqueued just
@@ -534,11 +604,13 @@ hs_status launch_fwd(const void *fn, dim3 grid, dim3 block, void **args, size_t 
 }
 
 // The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel.
-hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st)
+hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st, bool prewhitened = false)
 {
     if (!(p->d.flags & HS_FLAG_TRUNCATE_TAIL) || main_args.tail_tiles <= 0) return HS_OK;
     if (main_args.tail_tiles > 0x7fffffff) return HS_ERR_UNSUPPORTED;
-    const void *fn = fwd1d_tail_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0);
+    // on the pre-whitened copy the tail reads plain FP32
+    const void *fn = prewhitened ? fwd1d_tail_kernel(HS_F32, p->d.forms & 3, 0)
+                                 : fwd1d_tail_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0);
     if (!fn) return HS_ERR_UNSUPPORTED;
     Fwd1DArgs a = main_args;
     a.tile_counter = nullptr;
@@ -648,7 +720,7 @@ int64_t sweep_prefix(const hs_plan p) { return kSweepPrefixBands * std::max(1, p
 // shifted to its first tile, without the argmax reset (done once before the first chunk), the L2
 // prefetches (their input may not have arrived yet) or, but for the last chunk, the tail.
 hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_form_io *simple,
-                      const hs_form_io *greedy, void *ws, cudaStream_t st, int chunk = -1)
+                      const hs_form_io *greedy, void *ws, cudaStream_t st, int chunk = -1, bool prewhiten = false)
 {
     const int64_t B = p->d.dims == 1 ? p->d.num_spectra : 1;
     if (p->d.dims == 2) {
@@ -714,7 +786,17 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         a.pf_next = 0;
     }
     if ((p->d.forms & 3) == 0) return HS_OK;   // the optimal form runs through hs_run_optimal
-    const void *fn = fwd1d_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0, t.kernel);
+    // a whole pass of a whitening plan given a workspace (prewhiten) first writes the whitened
+    // input into it and then runs the plain FP32 pass on that copy: two gathers per loaded value
+    // (w[j] and p[j]) become one
+    const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
+    const bool pre = prewhiten && whiten && ws && chunk < 0 && t.kernel != 2;
+    if (pre) {
+        a.x = static_cast<const unsigned char *>(ws) + kWhitenedOffset;
+        a.w = nullptr;
+        a.elem_bytes = 4;
+    }
+    const void *fn = fwd1d_kernel(pre ? HS_F32 : p->d.dtype, p->d.forms & 3, (whiten && !pre) ? 1 : 0, t.kernel);
     if (!fn) return HS_ERR_UNSUPPORTED;
     // a whole pass clears the argmax keys (and the dynamic schedule's counter) with k_fwd_reset,
     // which the pass may overlap; a chunk of hs_run_host relies on the clear before its first chunk
@@ -722,7 +804,25 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     unsigned long long *g_key = greedy ? reinterpret_cast<unsigned long long *>(greedy->argmax) : nullptr;
     const bool dyn = t.kernel != 2 && t.dynamic && ws;
     bool after_reset = false;
-    if (chunk < 0 && (s_key || g_key || dyn)) {
+    if (pre) {
+        // the copy also clears the keys and the counter; the pass waits for the whole copy
+        const int64_t N = p->len[0];
+        const int64_t chunks = (N + 1023) / 1024 * B;
+        const unsigned grid_w = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(chunks, 8ll * p->sms)));
+        float *X = reinterpret_cast<float *>(static_cast<unsigned char *>(ws) + kWhitenedOffset);
+        unsigned long long *cnt = dyn ? static_cast<unsigned long long *>(ws) : nullptr;
+        const int32_t Bi = static_cast<int32_t>(B);
+        if (p->d.dtype == HS_F32)
+            k_prewhiten<float><<<grid_w, 256, 0, st>>>(static_cast<const float *>(spectra), w, X, p->d_in_off, Bi, N,
+                                                        s_key, g_key, cnt);
+        else if (p->d.dtype == HS_F16)
+            k_prewhiten<__half><<<grid_w, 256, 0, st>>>(static_cast<const __half *>(spectra), w, X, p->d_in_off, Bi,
+                                                         N, s_key, g_key, cnt);
+        else
+            k_prewhiten<__nv_bfloat16><<<grid_w, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(spectra), w, X,
+                                                                p->d_in_off, Bi, N, s_key, g_key, cnt);
+        HS_CUDA(cudaGetLastError());
+    } else if (chunk < 0 && (s_key || g_key || dyn)) {
         const int64_t rb = std::min<int64_t>(std::max<int64_t>((B + 255) / 256, 1), 64);
         k_fwd_reset<<<static_cast<unsigned>(rb), 256, 0, st>>>(s_key, g_key, (s_key || g_key) ? B : 0,
                                                               dyn ? static_cast<unsigned long long *>(ws) : nullptr);
@@ -754,7 +854,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, static_cast<int64_t>(t.ctas_per_sm) * p->sms);
     if (chunk < 0 && (t.kernel == 6 || t.kernel == 7) && (t.prefetch & 1) && p->l2_bytes > 0 && grid > 0) {
         // an input that fits in half of L2 is prefetched there by the first CTAs, one share each
-        const int64_t in_bytes = p->extent * elem_bytes(p->d.dtype);
+        const int64_t in_bytes = p->extent * a.elem_bytes;
         if (in_bytes <= p->l2_bytes / 2) {
             const int64_t ctas = std::min<int64_t>(grid, static_cast<int64_t>(p->sms) * 8);
             a.pf_bytes = in_bytes;
@@ -773,7 +873,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         hs_status ls = launch_fwd(fn, dim3(static_cast<unsigned>(grid)), dim3(t.threads), args, 0, st, after_reset);
         if (ls != HS_OK) return ls;
     }
-    return last ? launch_tail(p, a, st) : HS_OK;
+    return last ? launch_tail(p, a, st, pre) : HS_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1348,7 +1448,7 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     DeviceGuard guard(p->device);
     if (!guard.ok) return HS_ERR_CUDA;
-    if (!(p->d.flags & HS_FLAG_GRAPH)) return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+    if (!(p->d.flags & HS_FLAG_GRAPH)) return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st, -1, true);
 
     // graph replay: capture once per argument set on a private stream, launch on `st`
     std::lock_guard<std::mutex> lk(p->mu);
@@ -1361,11 +1461,11 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
     if (greedy) k.g = *greedy;
     if (!(p->gvalid && k == p->gkey)) {
         if (!p->cap && !cuda_ok(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)))
-            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st, -1, true);
         cudaGraph_t g = nullptr;
         bool ok = cuda_ok(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
         if (ok) {
-            hs_status es = enqueue_fwd(p, spectra, w, simple, greedy, workspace, p->cap);
+            hs_status es = enqueue_fwd(p, spectra, w, simple, greedy, workspace, p->cap, -1, true);
             ok = cuda_ok(cudaStreamEndCapture(p->cap, &g)) && es == HS_OK && g;
         }
         if (ok) {
@@ -1386,7 +1486,7 @@ hs_status hs_run(hs_plan p, const void *spectra, const float *w, const hs_form_i
         if (!ok) {   // capture failed: fall back to a direct launch
             cudaGetLastError();
             p->gvalid = false;
-            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st);
+            return enqueue_fwd(p, spectra, w, simple, greedy, workspace, st, -1, true);
         }
         p->gkey = k;
         p->gvalid = true;
@@ -1683,7 +1783,8 @@ hs_status hs_run_fixed_scratch(hs_plan p, const void *spectra, const float *w, c
     if (!p) return HS_ERR_INVALID_ARG;
     if (p->no_device) return HS_ERR_NO_DEVICE;
     // more scratch than the array (1D); a 2D plan runs without workspace (kernel 2 then runs as 1)
-    if (p->d.dims == 1 && fwd_workspace_bytes(p) > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;
+    // (a whitening plan runs here without its whitened copy: the pass multiplies as it loads)
+    if (p->d.dims == 1 && kWorkspaceBytes > kFixedScratchBytes) return HS_ERR_UNSUPPORTED;
     if (!spectra || !aligned(spectra, 16)) return HS_ERR_INVALID_ARG;
     const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
     if (whiten != (w != nullptr)) return HS_ERR_INVALID_ARG;

@@ -268,3 +268,38 @@ def test_bounded_wait_reports_timeout(hs, oracle_lib, limit_us):
     hs.check_device_error(plan)                    # the error word was cleared
     plan.close()
     run_case(hs, oracle_lib, [x], 16)              # and the device still computes
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("flags", [0, 128])
+def test_whitening_copy_equals_multiply_on_load(hs, oracle_lib, dtype, flags):
+    """A whitening plan given a workspace writes fl32(w p) into it and runs the plain FP32 pass on
+    that copy; without one (the fixed-scratch entry point) the pass multiplies as it loads.  Both
+    give the same outputs bit for bit (the truncated tail included), and the oracle agrees."""
+    N, B, H = 40013, 3, 16
+    xs = [synth.spectrum(N, 810 + i, [synth.Pulsar(91.3 + 7 * i, 0.05)]) for i in range(B)]
+    w = synth.whitening(N, 44)
+    if not flags:      # (the tail's oracle comparison with whitening is in test_gpu_tail.py)
+        assert run_case(hs, oracle_lib, xs, H, dtype=dtype, w=w) <= 4
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=[N] * B, dtype=dtype, flags=hs.FLAG_WHITENING | flags)
+    assert plan.workspace_bytes >= plan.extent * 4
+    buf = torch.zeros(plan.extent, dtype=TORCH_DT[dtype])
+    for s, x in enumerate(xs):
+        o = int(plan.input_offsets[s])
+        buf[o:o + N] = stored(x, dtype)[0]
+    xd, wd = buf.to(DEV), torch.from_numpy(w).to(DEV)
+    ns = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.SIMPLE, 1, H)]
+    ng = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
+    outs = []
+    for how in ("copy", "on load"):
+        s_io, g_io = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng)
+        if how == "copy":
+            hs.run(plan, xd, wd, s_io, g_io)
+        else:
+            hs.run_fixed_scratch(plan, xd, wd, s_io, g_io)
+        torch.cuda.synchronize()
+        hs.check_device_error(plan)
+        outs.append([s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    plan.close()
