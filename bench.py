@@ -69,7 +69,7 @@ KERNEL_SOURCES = {
     "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
-    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
+    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh", "hs_api.cu"],
 }
 
 
@@ -339,13 +339,26 @@ def time_steps(torch, step, K, stream, flush=None):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def traffic_entry(wl, tuning):
+    """The committed ncu capture of this workload's timed kernel (profiles/traffic.json holds one or
+    more per workload, one per captured launch shape) whose sources and launch shape are the ones
+    that ran; None when there is none."""
+    ents = (load_json(PROFILE_TRAFFIC) or {}).get(wl) or []
+    if isinstance(ents, dict):
+        ents = [ents]
+    h = kernel_hash(wl)
+    for e in ents:
+        if e.get("kernel_hash") == h and e.get("tuning") == tuning:
+            return e
+    return None
+
+
 def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
     """roofline entry; `traffic` = DRAM bytes per launch from the committed ncu capture of this
     workload, reported only while the kernel's sources and launch shape are those captured."""
     achieved = alg_bytes / (ms / 1e3) / 1e9
-    prof = load_json(PROFILE_TRAFFIC) or {}
-    pk = prof.get(wl) or {}
-    fresh = pk.get("kernel_hash") == kernel_hash(wl) and pk.get("tuning") == tuning
+    pk = traffic_entry(wl, tuning) or {}
+    fresh = bool(pk)
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": pk.get("dram_bytes_per_launch") if fresh else None,
             "algorithmic_bytes": int(alg_bytes), "bytes_basis": how, "peak_kind": peak_kind,
