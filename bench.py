@@ -9,6 +9,7 @@ CUDA events on the stream hs_run launches on.
 
 The same line carries a ``workloads`` object with every other configuration, each timed in the
 same run with its own roofline, clocks and CPU baseline (``--extras none`` skips them):
+  long16              the headline spectrum stored in FP16 (FP32 accumulation)
   batch / batch16     2048 uneven spectra (2^20..2^23 bins), H = 16, 5 % with a pulsar, one
                       launch replayed from a CUDA graph, launch shape autotuned (the line names it);
                       FP32 / FP16 storage (inputs 32 / 16 GB, larger than L2: no flush)
@@ -19,8 +20,8 @@ same run with its own roofline, clocks and CPU baseline (``--extras none`` skips
                       (torch.topk), hand-written adjoint to dL/dw
   table2              the paper's throughput configuration (Table 2): 1024 spectra x 131072 bins, H = 32,
                       greedy; also with every bin a fundamental (truncated tail), in Gbin/s
-Any of them (and long16 / longbf16, the headline spectrum in FP16 / BF16) can also be the
-headline of a run of its own (--workload).
+Any of them (and longbf16, the headline spectrum in BF16) can also be the headline of a run of
+its own (--workload).
 
 CPU baseline: the FP64 oracle on a bounded sample of the same input, on one thread (the oracle
 proper) and on every core of the host (the same source built with OpenMP over fundamentals,
@@ -821,7 +822,7 @@ WORKLOADS = {"long": wl_long, "long16": wl_long, "longbf16": wl_long, "batch": w
              "plane": wl_plane, "plane16": wl_plane, "planebf16": wl_plane, "grad": wl_grad, "table2": wl_table2}
 
 
-EXTRAS = ("batch", "batch16", "plane", "plane16", "grad", "table2")
+EXTRAS = ("long16", "batch", "batch16", "plane", "plane16", "grad", "table2")
 
 
 def reference_arm(args, rank, world):
