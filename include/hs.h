@@ -185,8 +185,11 @@ hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 /* Forward pass.  spectra: device input of the plan's dtype at the plan's offsets (2D: the plane).
  * w: device [N] float whitening weights (HS_FLAG_WHITENING) or NULL.  simple / greedy: the
  * forms' I/O (NULL for a form not in the plan).  workspace: >= hs_plan_workspace bytes or NULL
- * when that is 0.  Enqueues on `stream`; graph-capturable (it also resets argmax/workspace with
- * stream-ordered memsets). */
+ * when that is 0.  Enqueues on `stream`; graph-capturable.  A 1D pass first clears the argmax keys
+ * (and the dynamic schedule's counter) with a small kernel that the pass overlaps (programmatic
+ * dependent launch); a whitening plan given a workspace first writes its whitened copy there
+ * (which also clears them); a 2D pass clears its key with a stream-ordered memset.  Calls on one
+ * plan that share a workspace must not overlap on the GPU. */
 hs_status hs_run(hs_plan plan, const void *spectra, const float *w, const hs_form_io *simple,
                  const hs_form_io *greedy, void *workspace, void *stream);
 
