@@ -70,7 +70,7 @@ KERNEL_SOURCES = {
     "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
-    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh", "hs_api.cu"],
+    "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh", "hs_prewhiten.cuh"],
 }
 
 

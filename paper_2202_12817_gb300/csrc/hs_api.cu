@@ -16,6 +16,7 @@
 
 #include "hs_fwd2d_sweep.cuh"
 #include "hs_internal.cuh"
+#include "hs_prewhiten.cuh"
 
 using namespace hs;
 
@@ -502,83 +503,6 @@ const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
     return nullptr;
 }
 
-// A stored 16-bit value widened exactly to FP32.
-template <typename T>
-__device__ __forceinline__ float widen16(unsigned int bits);
-template <>
-__device__ __forceinline__ float widen16<__half>(unsigned int bits)
-{
-    return __half2float(__ushort_as_half(static_cast<unsigned short>(bits)));
-}
-template <>
-__device__ __forceinline__ float widen16<__nv_bfloat16>(unsigned int bits)
-{
-    return __uint_as_float(bits << 16);
-}
-
-// Clears the per-spectrum argmax keys of both forms and the dynamic schedule's tile counter before
-// a 1D pass.  Its first instruction lets the pass that follows it on the stream start at once
-// (programmatic dependent launch); the pass waits for this kernel only before its first argmax
-// update or tile-counter fetch, so the clear costs no serialisation gap.
-__global__ void k_fwd_reset(unsigned long long *s_key, unsigned long long *g_key, int64_t B,
-                            unsigned long long *counter)
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < B; i += stride) {
-        if (s_key) s_key[i] = 0ull;
-        if (g_key) g_key[i] = 0ull;
-    }
-    if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0ull;
-}
-
-// Whitened copy of a whitening plan's input: X[o_s + j] = fl32(w[j] p_s[j]) for every spectrum s
-// (offset o_s) and bin j < N, the product each pass kernel would form as it loads (the same single
-// rounding, so the pass on X gives the same outputs bit for bit).  Four bins per thread where the
-// input is 16-byte aligned (offsets and w are; N may leave a ragged tail).  Also clears the argmax
-// keys and the tile counter, as k_fwd_reset does.
-template <typename T>
-__global__ void __launch_bounds__(256) k_prewhiten(const T *p, const float *w, float *X, const int64_t *in_off,
-                                                   int32_t B, int64_t N, unsigned long long *s_key,
-                                                   unsigned long long *g_key, unsigned long long *counter)
-{
-    if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < B; i += blockDim.x) {
-            if (s_key) s_key[i] = 0ull;
-            if (g_key) g_key[i] = 0ull;
-        }
-        if (counter && threadIdx.x == 0) *counter = 0ull;
-    }
-    const int64_t cps = (N + 1023) / 1024;   // 1024-bin chunks per spectrum
-    const int64_t total = cps * B;
-    for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-        const int64_t sp = c / cps;
-        const int64_t j0 = (c - sp * cps) * 1024 + 4 * threadIdx.x;
-        const int64_t o = __ldg(in_off + sp);
-        if (j0 + 3 < N) {
-            const float4 wv = __ldg(reinterpret_cast<const float4 *>(w + j0));
-            float v0, v1, v2, v3;
-            if constexpr (sizeof(T) == 4) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(p + o + j0));
-                v0 = q.x; v1 = q.y; v2 = q.z; v3 = q.w;
-            } else {
-                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p + o + j0));
-                v0 = widen16<T>(q.x & 0xffffu); v1 = widen16<T>(q.x >> 16);
-                v2 = widen16<T>(q.y & 0xffffu); v3 = widen16<T>(q.y >> 16);
-            }
-            *reinterpret_cast<float4 *>(X + o + j0) =
-                make_float4(__fmul_rn(wv.x, v0), __fmul_rn(wv.y, v1), __fmul_rn(wv.z, v2), __fmul_rn(wv.w, v3));
-        } else {
-            for (int64_t j = j0; j < N && j < j0 + 4; ++j) {
-                float v;
-                if constexpr (sizeof(T) == 4) v = __ldg(reinterpret_cast<const float *>(p) + o + j);
-                else v = widen16<T>(__ldg(reinterpret_cast<const unsigned short *>(p) + o + j));
-                X[o + j] = __fmul_rn(__ldg(w + j), v);
-            }
-        }
-    }
-}
-
 // Launch of a 1D forward kernel; with `after_reset` it may start while k_fwd_reset (enqueued just
 // before it) still runs -- every 1D forward kernel waits (griddepcontrol.wait) before it touches
 // what the reset writes.
@@ -788,9 +712,10 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     if ((p->d.forms & 3) == 0) return HS_OK;   // the optimal form runs through hs_run_optimal
     // a whole pass of a whitening plan given a workspace (prewhiten) first writes the whitened
     // input into it and then runs the plain FP32 pass on that copy: two gathers per loaded value
-    // (w[j] and p[j]) become one
+    // (w[j] and p[j]) become one.  The copy's float4 stores need a 16-byte aligned workspace; with
+    // another, the pass multiplies as it loads.
     const bool whiten = (p->d.flags & HS_FLAG_WHITENING) != 0;
-    const bool pre = prewhiten && whiten && ws && chunk < 0 && t.kernel != 2;
+    const bool pre = prewhiten && whiten && ws && aligned(ws, 16) && chunk < 0 && t.kernel != 2;
     if (pre) {
         a.x = static_cast<const unsigned char *>(ws) + kWhitenedOffset;
         a.w = nullptr;
@@ -964,7 +889,7 @@ hs_status autotune(hs_plan p)
     hs_form_io fs{}, fg{};
     const size_t out_bytes = static_cast<size_t>(F) * (4 + 1 + 4 + 1) + 256;
     if (!cuda_ok(cudaMalloc(&x, ext * elem_bytes(sd.dtype) + 64)) || !cuda_ok(cudaMalloc(&tmp, ext * 4 + 64)) ||
-        !cuda_ok(cudaMalloc(&w, lens[0] * 4 + 64)) || !cuda_ok(cudaMalloc(&ws, kWorkspaceBytes)) ||
+        !cuda_ok(cudaMalloc(&w, lens[0] * 4 + 64)) || !cuda_ok(cudaMalloc(&ws, fwd_workspace_bytes(sp))) ||
         !cuda_ok(cudaMalloc(&outs, out_bytes)) || !cuda_ok(cudaMalloc(&norm, 4 * H * 4)) ||
         !cuda_ok(cudaMalloc(&flush, flush_bytes)) ||
         !cuda_ok(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) || !cuda_ok(cudaEventCreate(&e0)) ||
@@ -1025,7 +950,9 @@ hs_status autotune(hs_plan p)
                 hs_tuning t{kernel, threads, 1, 0, 0, 0, 0, pf, 0};
                 if (sched >= 1) {
                     int occ = 0;
-                    const void *fn = fwd1d_kernel(sd.dtype, sd.forms & 3, (sd.flags & HS_FLAG_WHITENING) ? 1 : 0, kernel);
+                    // a whitening plan runs its pass on the whitened FP32 copy
+                    const bool wh = (sd.flags & HS_FLAG_WHITENING) != 0;
+                    const void *fn = fwd1d_kernel(wh ? HS_F32 : sd.dtype, sd.forms & 3, 0, kernel);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
                     if (occ < 1) continue;
                     t.ctas_per_sm = occ;
@@ -1045,7 +972,7 @@ hs_status autotune(hs_plan p)
         for (int rep = 0; rep < 4; ++rep) {
             cudaMemsetAsync(flush, rep & 0xff, flush_bytes, s);
             cudaEventRecord(e0, s);
-            if (enqueue_fwd(sp, x, wp, ps, pg, ws, s) != HS_OK) { result = HS_ERR_CUDA; goto done; }
+            if (enqueue_fwd(sp, x, wp, ps, pg, ws, s, -1, true) != HS_OK) { result = HS_ERR_CUDA; goto done; }
             cudaEventRecord(e1, s);
             if (!cuda_ok(cudaEventSynchronize(e1))) { result = HS_ERR_CUDA; goto done; }
             float ms = 0.f;

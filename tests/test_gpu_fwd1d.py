@@ -235,6 +235,16 @@ def test_autotune(hs, oracle_lib):
     run_case(hs, oracle_lib, xs, 16, flags=hs.FLAG_AUTOTUNE)
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_autotune_whitening(hs, oracle_lib, dtype):
+    """The autotuner times a whitening plan's candidates on the path hs_run takes (the whitened
+    copy, then the plain FP32 pass) and the chosen shape still agrees with the oracle."""
+    N = 1 << 18
+    w = synth.whitening(N, 9)
+    xs = [synth.spectrum(N, 60 + i, [synth.Pulsar(501.2 + 13 * i, 0.06)]) for i in range(4)]
+    run_case(hs, oracle_lib, xs, 16, w=w, dtype=dtype, flags=hs.FLAG_AUTOTUNE)
+
+
 def test_long_spectrum_full_size(hs, oracle_lib):
     """The 2^23-bin, H = 32 single-spectrum workload in the default launch configuration."""
     x = synth.long_spectrum()
@@ -300,6 +310,37 @@ def test_whitening_copy_equals_multiply_on_load(hs, oracle_lib, dtype, flags):
         torch.cuda.synchronize()
         hs.check_device_error(plan)
         outs.append([s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    plan.close()
+
+
+@pytest.mark.parametrize("tuning", [None, dict(kernel=0, threads=128, ctas_per_sm=4, dynamic=1)])
+def test_whitening_workspace_off_16_bytes(hs, tuning):
+    """A workspace that is 8- but not 16-byte aligned cannot take the whitened copy's 16-byte
+    stores: the pass then multiplies as it loads (the dynamic schedule's counter still lives at
+    its start), with the same outputs bit for bit as with an aligned workspace."""
+    N, B, H = 40013, 2, 16
+    xs = [synth.spectrum(N, 850 + i, [synth.Pulsar(61.3 + 5 * i, 0.05)]) for i in range(B)]
+    plan = hs.Plan(H, hs.SIMPLE | hs.GREEDY, lengths=[N] * B, flags=hs.FLAG_WHITENING)
+    if tuning:
+        plan.tuning = tuning
+    buf = torch.zeros(plan.extent, dtype=torch.float32)
+    for s, x in enumerate(xs):
+        o = int(plan.input_offsets[s])
+        buf[o:o + N] = torch.from_numpy(x)
+    xd, wd = buf.to(DEV), torch.from_numpy(synth.whitening(N, 47)).to(DEV)
+    ns = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.SIMPLE, 1, H)]
+    ng = [torch.from_numpy(a).to(DEV) for a in hs.norm_exponential(hs.GREEDY, 1, H)]
+    big = torch.zeros(plan.workspace_bytes + 256, dtype=torch.uint8, device=DEV)
+    outs = []
+    for ws in (big[:plan.workspace_bytes], big[8:8 + plan.workspace_bytes]):
+        s_io, g_io = plan.alloc_form(*ns, path=False), plan.alloc_form(*ng)
+        hs.run(plan, xd, wd, s_io, g_io, workspace=ws)
+        torch.cuda.synchronize()
+        hs.check_device_error(plan)
+        outs.append([s_io.snr, s_io.best_h, s_io.argmax, g_io.snr, g_io.best_h, g_io.path, g_io.argmax])
+    assert big.data_ptr() % 256 == 0
     for a, b in zip(*outs):
         assert torch.equal(a, b)
     plan.close()
