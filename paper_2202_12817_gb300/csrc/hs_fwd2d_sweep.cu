@@ -28,18 +28,6 @@ __device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map,
         : "memory");
 }
 
-// Chain state goes to L2 (bypassing L1); other CTAs read it back with bulk copies.
-__device__ __forceinline__ void st_state(int4 *p, int4 v)
-{
-    asm volatile("st.global.cg.v4.s32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void consumer_sync_id(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
     unsigned v;
@@ -83,22 +71,6 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, volat
         if (*dead) return false;
         if (global_ns() - t0 > kWaitNs) return false;
     }
-}
-
-// Named barrier `id` over n threads that returns the OR of every participant's predicate, so a
-// decision to stop is the same for all of them.
-__device__ __forceinline__ bool bar_or(int id, int n, bool pred)
-{
-    unsigned r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(static_cast<unsigned>(pred)), "r"(id), "r"(n)
-        : "memory");
-    return r != 0u;
 }
 
 // Push finished band jb (-1: no more) on the publisher's ring, waiting (bounded) while it is full.
@@ -146,6 +118,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
     __shared__ int s_ring[kSweepRing];                  // finished bands, compute -> publisher
     __shared__ volatile unsigned s_head, s_tail;        // ring entries pushed / published
     __shared__ volatile int s_dead;
+    __shared__ unsigned s_cnt[kSweepMaxStages];         // compute warps done with buffer b's task
 
     const Fwd2DArgs &a = s.a;
     const int H = a.H, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -168,6 +141,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         s_head = 0u;
         s_tail = 0u;
         s_dead = 0;
+        for (int i = 0; i < kSweepMaxStages; ++i) s_cnt[i] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -288,13 +262,26 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 // dependencies: poll (bounded) the flags that were still clear when prepared; the
                 // bulk copies then read through the async proxy what other CTAs stored through the
                 // generic proxy, after the flags were acquired
+                bool unmet = false;
                 if (p_dep >= 0 && p_flag == 0u) {
                     const unsigned long long t0 = global_ns();
                     while (ld_acquire(done + p_dep) == 0u) {
-                        if (*reinterpret_cast<volatile int *>(a.err) == kErrTimeout) break;
-                        if (global_ns() - t0 > kWaitNs) { set_error(a.err, kErrTimeout); break; }
+                        if (*reinterpret_cast<volatile int *>(a.err) == kErrTimeout) { unmet = true; break; }
+                        if (global_ns() - t0 > kWaitNs) { set_error(a.err, kErrTimeout); unmet = true; break; }
                         __nanosleep(64);
                     }
+                }
+                // a band whose dependencies were not met would read chain state that was never
+                // written (its drift could point outside the staged tile): the CTA stops instead,
+                // handing the compute warps the end marker
+                if (__any_sync(0xffffffffu, unmet)) {
+                    if (lane == 0) {
+                        s_dead = 1;
+                        hdr[b].task = total;
+                        mbar_arrive(&full[b]);
+                    }
+                    __syncwarp();
+                    break;
                 }
                 __syncwarp();
                 asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -354,24 +341,27 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         }
         __syncwarp();
     } else {
-        // ---- compute warps: run task k from buffer k % nbuf, order by order
+        // ---- compute warps: run task k from buffer k % nbuf.  Each warp goes through the tasks on
+        // its own (no barrier across the compute warps): the last warp to finish a task releases
+        // its buffer to the control warp and hands the band to the publisher.
         const int ctid = tid - 64;
+        const unsigned NW = static_cast<unsigned>(NC >> 5);
         const int P = s.Wb + 2 * kSweepHalo;
+        int rot = 0;   // events of the bands so far, mod NC (the bands' events form one round-robin)
         for (long long k = 0;; ++k) {
             const int b = static_cast<int>(k % nbuf);
             const uint32_t u = static_cast<uint32_t>(k / nbuf);
             const bool lost = !wait_phase(&full[b], u & 1u, &s_dead);
-            if (bar_or(1, NC, lost)) {
-                if (ctid == 0) { set_error(a.err, kErrTimeout); s_dead = 1; }
+            if (__any_sync(0xffffffffu, lost)) {
+                if (lane == 0) { set_error(a.err, kErrTimeout); s_dead = 1; }
                 break;
             }
             const BandHdr &hd = hdr[b];
             const long long t = hd.task;
+            int jb = -2;   // what the last warp hands to the publisher: band j, -1 (end) or nothing
             if (t >= total) {
-                if (ctid == 0) push_finished(s_ring, s_head, s_tail, -1, &s_dead, a.err);
-                break;
-            }
-            if (t < s.n_prefix) {
+                jb = -1;
+            } else if (t < s.n_prefix) {
                 // prefix task: chains f < f_s, each carried in registers through all orders
                 const long long npf = s.f_s - a.f_lo;
                 const long long c = t * NC + ctid;
@@ -396,72 +386,83 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     const unsigned long long kk = argmax_key(ch.best, o);
                     key = kk > key ? kk : key;
                 }
-                consumer_sync_id(1, NC);
-                if (ctid == 0) mbar_arrive(&empty[b]);
-                continue;
-            }
-            const int j = static_cast<int>(t - s.n_prefix);
-            const unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
-            const T *tile = reinterpret_cast<const T *>(buf);
-            const int4 *sst = reinterpret_cast<const int4 *>(buf + s.tile_bytes);
-            const int col0 = static_cast<int>(hd.c0 - kSweepHalo);   // plane column of tile column 0
-            // the band's events of every order as one index space e in [0, ev[H]): order h holds
-            // [ev[h-1], ev[h]), within it event i is chain (fa + i % nf, z_lo + i / nf).  Every
-            // event of a band is independent of the others (order h of chain f anchors at h f, order
-            // h + 1 at h f + f >= h f + Wb: a later band), so the orders need no barrier between them
-            // and no thread idles while the high orders, which hold few events, run.  A thread's
-            // events increase, so its order h only moves up.
-            const int E = hd.ev[H];
-            int h = 0, e_hi = 0, nf = 0, fa = 0, so = 0, zrow = 0;
-            unsigned long long mg = 0ull;
-            float rsh = 0.f, mursh = 0.f;
-            for (int e = ctid; e < E; e += NC) {
-                if (e >= e_hi) {
-                    do {
-                        ++h;
-                        e_hi = hd.ev[h];
-                    } while (e >= e_hi);
-                    nf = hd.nf[h - 1];
-                    fa = static_cast<int>(hd.fa[h - 1]);
-                    so = hd.soff[h - 1];
-                    mg = hd.mg[h - 1];
-                    rsh = rs[h - 1];
-                    mursh = murs[h - 1];
-                    zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
-                }
-                const unsigned i = static_cast<unsigned>(e - hd.ev[h - 1]);
-                const int zi = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
-                const int fi = static_cast<int>(i) - zi * nf;
-                const int f = fa + fi;
-                Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
-                if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
-                const int cf = h * f + ch.df;
-                const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
-                const T *p0 = tile + cr * P + (cf - 1 - col0);
-                float v9[9];
+            } else {
+                jb = static_cast<int>(t - s.n_prefix);
+                const unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
+                const T *tile = reinterpret_cast<const T *>(buf);
+                const int4 *sst = reinterpret_cast<const int4 *>(buf + s.tile_bytes);
+                const int col0 = static_cast<int>(hd.c0 - kSweepHalo);   // plane column of tile column 0
+                // the band's events of every order as one index space e in [0, ev[H]): order h holds
+                // [ev[h-1], ev[h]), within it event i is chain (fa + i % nf, z_lo + i / nf).  Every
+                // event of a band is independent of the others (order h of chain f anchors at h f,
+                // order h + 1 at h f + f >= h f + Wb: a later band), so the orders need no barrier
+                // between them.  The events of successive bands continue one round-robin over the
+                // compute threads, so no thread idles at the end of a band.  A thread's events
+                // increase, so its order h only moves up.
+                const int E = hd.ev[H];
+                int e = ctid - rot;
+                if (e < 0) e += NC;
+                rot = (rot + E) % NC;
+                int h = 0, e_hi = 0, nf = 0, fa = 0, so = 0, zrow = 0;
+                unsigned long long mg = 0ull;
+                float rsh = 0.f, mursh = 0.f;
+                for (; e < E; e += NC) {
+                    if (e >= e_hi) {
+                        do {
+                            ++h;
+                            e_hi = hd.ev[h];
+                        } while (e >= e_hi);
+                        nf = hd.nf[h - 1];
+                        fa = static_cast<int>(hd.fa[h - 1]);
+                        so = hd.soff[h - 1];
+                        mg = hd.mg[h - 1];
+                        rsh = rs[h - 1];
+                        mursh = murs[h - 1];
+                        zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
+                    }
+                    const unsigned i = static_cast<unsigned>(e - hd.ev[h - 1]);
+                    const int zi = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
+                    const int fi = static_cast<int>(i) - zi * nf;
+                    const int f = fa + fi;
+                    Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
+                    if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
+                    const int cf = h * f + ch.df;
+                    const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
+                    const T *p0 = tile + cr * P + (cf - 1 - col0);
+                    float v9[9];
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
+                    for (int r = 0; r < 3; ++r)
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
-                chain2d_step(ch, h, v9, rsh, mursh);
-                if (h == H) {
-                    const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
-                    a.g.snr[o] = ch.best;
-                    a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
-                    if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
-                    const unsigned long long kx = argmax_key(ch.best, o);
-                    key = kx > key ? kx : key;
-                } else {
-                    st_state(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
+                        for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
+                    chain2d_step(ch, h, v9, rsh, mursh);
+                    if (h == H) {
+                        const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
+                        a.g.snr[o] = ch.best;
+                        a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
+                        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
+                        const unsigned long long kx = argmax_key(ch.best, o);
+                        key = kx > key ? kx : key;
+                    } else {
+                        __stcg(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
+                    }
                 }
             }
-            // every compute thread is done with the buffer and has issued its stores: release the
-            // buffer to the control warp and hand the band to the publisher
-            consumer_sync_id(1, NC);
-            if (ctid == 0) {
-                mbar_arrive(&empty[b]);
-                push_finished(s_ring, s_head, s_tail, j, &s_dead, a.err);
+            // this warp is done with the buffer and its stores are issued; the last warp of the
+            // task (its count, taken with release / acquire fences at block scope, orders every
+            // warp's stores before it) releases the buffer and hands the band to the publisher
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const unsigned c = atomicAdd(&s_cnt[b], 1u);
+                if (c + 1u == NW) {
+                    __threadfence_block();
+                    s_cnt[b] = 0u;
+                    if (jb != -2) push_finished(s_ring, s_head, s_tail, jb, &s_dead, a.err);
+                    if (jb != -1) mbar_arrive(&empty[b]);
+                }
             }
+            __syncwarp();
+            if (t >= total) break;
         }
     }
     __syncthreads();

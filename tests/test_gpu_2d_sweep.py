@@ -136,3 +136,28 @@ def test_sweep_stages(hs, oracle_lib, stages, dtype):
     z0 = 30
     pl = synth.plane(96000, 2 * z0 + 1, z0, 170 + stages, synth.random_tracks(4, 96000, 23, f_lo=50, zmax=3))
     run_2d(hs, oracle_lib, pl, z0, 8, dtype=dtype, tuning=dict(kernel=2, threads=512, stage_kb=2, stages=stages))
+
+
+def test_sweep_stops_on_a_recorded_timeout(hs):
+    """A timeout already recorded in the plan's error word (as after another CTA's wait ran out):
+    a CTA whose next band still waits on a dependency stops instead of reading chain state that
+    was never written.  The pass ends, reports HS_ERR_DEVICE_TIMEOUT, and the plan then gives the
+    outputs of kernel 1 again."""
+    n_freq, z0, H = 1 << 18, 100, 8
+    pl_dev = torch.from_numpy(synth.plane(n_freq, 2 * z0 + 1, z0, 335, synth.random_tracks(4, n_freq, 336))).to(DEV)
+    ref_plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=2 * z0 + 1, z0_row=z0)
+    ref_plan.tuning = dict(kernel=1, threads=256)
+    ref = _outputs(hs, ref_plan, pl_dev, H)
+    plan = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=2 * z0 + 1, z0_row=z0)
+    plan.tuning = dict(kernel=2, threads=512)
+    mu, sg = hs.norm_exponential(2, 2, H, True, 2.0)
+    g = plan.alloc_form(torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
+    hs.selftest_timeout(plan, 1000)          # records the timeout; the pass is queued after it
+    hs.run(plan, pl_dev, None, None, g)
+    with pytest.raises(hs.HSError) as e:
+        hs.check_device_error(plan)
+    assert e.value.status == 6               # HS_ERR_DEVICE_TIMEOUT
+    for a, b in zip(ref, _outputs(hs, plan, pl_dev, H)):
+        assert torch.equal(a, b)
+    plan.close()
+    ref_plan.close()
