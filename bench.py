@@ -67,7 +67,8 @@ KERNEL_SOURCES = {
     "batch": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
     "batch16": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f16.cu", "hs_internal.cuh"],
     "table2": ["hs_fwd1d.cuh", "hs_fwd1d_win.cuh", "hs_fwd1d_pair.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh"],
-    "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
+    "plane": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd2d_sweep.cu", "hs_fwd2d_sweep.cuh", "hs_fwd1d.cuh",
+              "hs_fwd1d_win.cuh", "hs_internal.cuh"],
     "plane16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "planebf16": ["hs_fwd2d.cu", "hs_fwd2d.cuh", "hs_fwd1d.cuh", "hs_internal.cuh"],
     "grad": ["hs_bwd1d.cu", "hs_fwd1d.cuh", "hs_fwd1d_f32.cu", "hs_internal.cuh", "hs_prewhiten.cuh"],

@@ -174,11 +174,14 @@ hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
  * all orders of all chains anchored there run from it, the chain state waiting in the workspace
  * between orders (plane DRAM reads about 2.4x lower than kernel 1 on a 201 x 2^21 plane).
  * Kernel 2 takes threads 256, 512 or 1024 (two warps of which control and publish), stage_kb =
- * band width / 16 (0: 64 columns for FP32, 96 for 16-bit storage), stages = 2..4 buffers (0: 2),
+ * band width / 16 (0: 112 columns for FP32, 176 for 16-bit storage, or the widest narrower
+ * multiple of 16 the plane takes), stages = 2..4 buffers of one band's tile each (0: 2),
  * ctas_per_sm 0..4, producers 0..64 (chains f < 64 max(1, producers) band widths run whole in
- * registers before the sweep takes over; 0: 64 band widths); it needs rows whose byte stride is a multiple of 16, at most 256 reachable
- * rows, no HS_FLAG_CHECKED, and the workspace (without one, hs_run and hs_run_fixed_scratch run
- * it as kernel 1, with the same outputs bit for bit). */
+ * registers before the sweep takes over; 0: 64 band widths); it needs rows whose byte stride is
+ * a multiple of 16, at most 256 reachable rows, no HS_FLAG_CHECKED, and the workspace (without
+ * one, hs_run and hs_run_fixed_scratch run it as kernel 1, with the same outputs bit for bit).
+ * The default is kernel 1, except for FP32 planes larger than the device's L2 that the sweep
+ * takes: kernel 2 with 1024 threads and producers 5. */
 hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
 hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 

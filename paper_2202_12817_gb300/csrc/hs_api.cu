@@ -133,11 +133,14 @@ constexpr int64_t kSweepPrefixBands = 64;       // chains f < 64 Wb run whole in
 // Band width (anchor columns) when the tuning leaves it open: the two buffers (plane tile + the
 // band's chain state) of a ~200-row plane at H = 8 then take ~206 KB for FP32 (64 columns) and
 // ~209 KB for 16-bit storage (96 columns), one 512-thread CTA per SM.
-int sweep_default_wb(int dtype) { return dtype == HS_F32 ? 64 : 96; }
+// Band width of the column sweep when tuning.stage_kb is 0.  On the 201 x 2^21 plane, H = 8, 1024
+// threads: FP32 112 columns 547 us (64: 790 us with 512 threads, 128: 640 us), FP16 176 columns
+// 519 us (112: 534 us).
+int sweep_default_wb(int dtype) { return dtype == HS_F32 ? 112 : 176; }
 
 struct SweepGeom {
     bool ok = false;
-    int Wb = 0, r_lo = 0, nr = 0, box_bytes = 0, tile_bytes = 0, buf_bytes = 0, nbuf = 0;
+    int Wb = 0, r_lo = 0, nr = 0, box_bytes = 0, buf_bytes = 0, nbuf = 0;
     int64_t f_s = 0, band_lo = 0, nbands = 0, n_prefix = 0;
     size_t state_bytes = 0, sync_bytes = 0;
 };
@@ -166,11 +169,7 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t
     if (nr < 3 || nr > kSweepMaxBox) return g;
     const int64_t nz = p->z_hi - p->z_lo + 1;
     const int64_t box = nr * (Wb + 2 * kSweepHalo) * eb;
-    const int64_t tile = (box + 127) / 128 * 128;
-    // a band holds at most ceil(Wb / h) chains of order h, each with nz states (orders >= 2)
-    int64_t state_cap = 0;
-    for (int64_t h = 2; h <= H; ++h) state_cap += (Wb + h - 1) / h * nz * 16;
-    const int64_t buf = (tile + state_cap + 127) / 128 * 128;
+    const int64_t buf = (box + 127) / 128 * 128;   // one buffer: the band's staged plane tile
     if (nbuf < 2 || nbuf > kSweepMaxStages || nbuf * buf + kSweepStaticSmem > kSweepSmemLimit) return g;
     const int64_t f_s = std::max<int64_t>(p->f_lo, prefix_bands * Wb);
     if (f_s > p->f_hi) return g;
@@ -180,7 +179,6 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t
     g.r_lo = static_cast<int>(rmin);
     g.nr = static_cast<int>(nr);
     g.box_bytes = static_cast<int>(box);
-    g.tile_bytes = static_cast<int>(tile);
     g.buf_bytes = static_cast<int>(buf);
     g.nbuf = nbuf;
     g.f_s = f_s;
@@ -191,6 +189,15 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t
     g.sync_bytes = (static_cast<size_t>(2 + g.nbands) * 4 + 255) / 256 * 256;
     g.ok = true;
     return g;
+}
+
+// Band width for tuning.stage_kb = 0: the default, or the widest narrower multiple of 16 that the
+// plane takes (on a narrow plane no chain may lie beyond 64 default band widths).
+int sweep_auto_wb(const hs_plan p, int threads, int nbuf, int producers)
+{
+    for (int wb = sweep_default_wb(p->d.dtype); wb >= 16; wb -= 16)
+        if (sweep_geom(p, wb, threads, nbuf, kSweepPrefixBands * std::max(1, producers)).ok) return wb;
+    return sweep_default_wb(p->d.dtype);
 }
 
 // Forward workspace: the dynamic schedule's tile counter (1D); the sweep's chain state and band
@@ -605,7 +612,7 @@ hs_status launch_sweep(const hs_plan p, const Fwd2DArgs &a, const SweepGeom &g, 
     s.r_lo = g.r_lo;
     s.nr = g.nr;
     s.box_bytes = g.box_bytes;
-    s.tile_bytes = g.tile_bytes;
+    s.nfs = p->f_hi - g.f_s + 1;
     s.buf_bytes = g.buf_bytes;
     s.nbuf = g.nbuf;
     s.state = static_cast<int4 *>(ws);
@@ -630,11 +637,12 @@ hs_status launch_sweep(const hs_plan p, const Fwd2DArgs &a, const SweepGeom &g, 
 
 // Band width of the sweep under the plan's tuning (stage_kb = width / 16; 0 = default) and its
 // buffers (stages; 0 = 2).
+int sweep_stages(const hs_plan p) { return p->tun.stages > 0 ? p->tun.stages : 2; }
 int sweep_wb(const hs_plan p)
 {
-    return p->tun.stage_kb > 0 ? 16 * p->tun.stage_kb : sweep_default_wb(p->d.dtype);
+    return p->tun.stage_kb > 0 ? 16 * p->tun.stage_kb
+                               : sweep_auto_wb(p, p->tun.threads, sweep_stages(p), p->tun.producers);
 }
-int sweep_stages(const hs_plan p) { return p->tun.stages > 0 ? p->tun.stages : 2; }
 // Chains f < prefix bands x Wb run whole in registers (prefix tasks); tuning.producers scales the
 // default 64 bands (0 or 1: 64, k: 64 k).
 int64_t sweep_prefix(const hs_plan p) { return kSweepPrefixBands * std::max(1, p->tun.producers); }
@@ -1210,7 +1218,8 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         p->total_fund = (p->f_hi - p->f_lo + 1) * (p->z_hi - p->z_lo + 1);
         p->extent = d.n_freq * d.n_rows;
         p->path_bytes = 4;
-        // z rows fastest: 0.632 ms vs 0.674 ms (f-tiles fastest) on the 201 x 2^21 plane, H = 8
+        // z rows fastest: 0.632 ms vs 0.674 ms (f-tiles fastest) on the 201 x 2^21 plane, H = 8; an
+        // FP32 plane larger than the device's L2 takes the column sweep instead (below)
         p->tun = hs_tuning{1, 256, 1, 0, 0, 0, 0, 0, 0};
         p->len.assign(1, p->extent);
         p->in_off.assign(2, 0);
@@ -1237,6 +1246,14 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         // the default launch shape depends on whether the input fits in this device's L2
         p->tun = default_tuning(p);
         compute_tiles(p);
+    } else if (d.dtype == HS_F32 && p->extent * 4 > static_cast<int64_t>(p->l2_bytes)) {
+        // an FP32 plane larger than L2 runs the column sweep where it applies: 547 us vs 649 us
+        // for kernel 1 on the 201 x 2^21 plane, H = 8 (112-column bands, 1024 threads, chains
+        // f < 320 band widths in registers first).  16-bit planes keep kernel 1 (428 us vs 519 us:
+        // half the bytes make kernel 1's re-reads cheaper, while the sweep's cost barely changes).
+        const hs_tuning sw{2, 1024, 1, 0, 0, 0, 0, 0, 5};
+        const SweepGeom g = sweep_geom(p, sweep_default_wb(d.dtype), sw.threads, 2, kSweepPrefixBands * sw.producers);
+        if (g.ok && g.state_bytes + g.sync_bytes <= fwd_workspace_bytes(p)) p->tun = sw;
     }
     const size_t B1 = p->in_off.size();
     if (!cuda_ok(cudaMalloc(&p->d_in_off, sizeof(int64_t) * B1)) ||
@@ -1342,7 +1359,8 @@ hs_status hs_plan_set_tuning(hs_plan p, const hs_tuning *t)
             if ((t->threads != 256 && t->threads != 512 && t->threads != 1024) || t->ctas_per_sm < 0 || t->ctas_per_sm > 4 ||
                 t->stage_kb < 0 || t->stages < 0 || t->stages == 1 || t->stages > kSweepMaxStages)
                 return HS_ERR_INVALID_ARG;
-            const int wb = t->stage_kb > 0 ? 16 * t->stage_kb : sweep_default_wb(p->d.dtype);
+            const int wb = t->stage_kb > 0 ? 16 * t->stage_kb
+                                           : sweep_auto_wb(p, t->threads, t->stages > 0 ? t->stages : 2, t->producers);
             const SweepGeom g = sweep_geom(p, wb, t->threads, t->stages > 0 ? t->stages : 2,
                                            kSweepPrefixBands * std::max(1, t->producers));
             if (!g.ok || g.state_bytes + g.sync_bytes > fwd_workspace_bytes(p)) return HS_ERR_UNSUPPORTED;

@@ -17,6 +17,31 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first()
     return p;
 }
 
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Chain state between orders lives in L2 (L1 bypassed: other CTAs write it), kept there ahead of
+// the streaming plane tiles by the `pol` eviction hint.
+__device__ __forceinline__ int4 ld_state(const int4 *p, uint64_t pol)
+{
+    int4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_state(int4 *p, int4 v, uint64_t pol)
+{
+    asm volatile("st.global.cg.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // 2D tensor copy of the box at (x, y) into shared memory, completing on `bar` (expect-tx).
 __device__ __forceinline__ void tensor_g2s_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
                                               uint64_t policy)
@@ -98,7 +123,6 @@ struct BandHdr {
     long long c0;              // first anchor column of the band
     long long fa[kMaxH2D];     // order h = k + 1 holds chains [fa[k], fa[k] + nf[k]), all z
     int nf[kMaxH2D];
-    int soff[kMaxH2D];         // int4 offset of order h's state segment in the buffer
     int ev[kMaxH2D + 1];       // events of orders < h: order h's events are [ev[h-1], ev[h])
     unsigned long long mg[kMaxH2D];  // floor(2^32 / nf) + 1: i / nf = (i mg) >> 32 for the event
                                      // index i of an order (i nf < 2^32)
@@ -112,7 +136,8 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
     extern __shared__ __align__(128) unsigned char dyn[];
     __shared__ float rs[kMaxH2D], murs[kMaxH2D];
     __shared__ unsigned long long red[32];
-    // full[b]: the plane tile and the chain state of buffer b's band have landed
+    // full[b]: buffer b's plane tile has landed and the bands its chains' earlier orders lie in
+    // are done (two arrivals of the control warp: the copy's, and one after the dependencies)
     __shared__ __align__(8) uint64_t full[kSweepMaxStages], empty[kSweepMaxStages];
     __shared__ BandHdr hdr[kSweepMaxStages];
     __shared__ int s_ring[kSweepRing];                  // finished bands, compute -> publisher
@@ -135,7 +160,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
     const int nbuf = s.nbuf;
     if (tid == 0) {
         for (int i = 0; i < nbuf; ++i) {
-            mbar_init(&full[i], 1);
+            mbar_init(&full[i], 2);
             mbar_init(&empty[i], 1);
         }
         s_head = 0u;
@@ -149,10 +174,11 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
 
     if (warp == 0) {
         // ---- control warp: task k goes to buffer b = k % nbuf (free once the compute warps
-        // finished task k - nbuf).  Once the bands holding the previous orders of the band's
-        // chains are done it copies the band's plane tile and chain state into the buffer.
-        // Tickets are claimed one task ahead, and the next band's table is built and its
-        // dependency flags are read while the current band's copies are in flight.
+        // finished task k - nbuf).  It starts the copy of the band's plane tile into the buffer,
+        // then waits until the bands holding the previous orders of the band's chains are done
+        // (the compute warps read those chains' state from global memory).  Tickets are claimed
+        // one task ahead, and the next band's table is built and its dependency flags are read
+        // while the current band's copy is in flight.
         const uint64_t pol_plane = l2_policy_evict_first();
         const unsigned Wb = static_cast<unsigned>(s.Wb), band_lo = static_cast<unsigned>(s.band_lo);
         const unsigned f_s = static_cast<unsigned>(s.f_s), f_end = static_cast<unsigned>(f_hi + 1);
@@ -165,7 +191,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         // holding order h - 1 of order h's chains (p_dep = -1: none) with its flag as read
         long long pt = 0;
         unsigned p_fa = 0, p_nf = 0, p_flag = 1u;
-        int p_c0 = 0, p_sinc = 0, p_states = 0, p_dep = -1;
+        int p_c0 = 0, p_dep = -1;
         auto prepare = [&](long long t) {
             pt = t;
             p_nf = 0;
@@ -188,16 +214,6 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     dhi = static_cast<int>((h - 1) * (fb - 1) / Wb - band_lo);
                 }
             }
-            // inclusive prefix over the orders of their state entries (orders >= 2)
-            const int scnt = lane > 0 ? static_cast<int>(p_nf) * nz : 0;
-            int sinc = scnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int w = __shfl_up_sync(0xffffffffu, sinc, o);
-                if (lane >= o) sinc += w;
-            }
-            p_sinc = sinc;
-            p_states = __shfl_sync(0xffffffffu, sinc, 31);
             p_c0 = static_cast<int>(c0);
             const int src = (lane >> 1) + 1 < kMaxH2D ? (lane >> 1) + 1 : 0;   // order h = src + 1 >= 2
             const int lo = __shfl_sync(0xffffffffu, dlo, src), hi = __shfl_sync(0xffffffffu, dhi, src);
@@ -236,10 +252,11 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 if (lane == 0) {
                     hdr[b].task = t;
                     mbar_arrive(&full[b]);
+                    mbar_arrive(&full[b]);
                 }
                 if (t >= total) break;
             } else {
-                const int cnt = static_cast<int>(p_nf) * nz, scnt = lane > 0 ? cnt : 0;
+                const int cnt = static_cast<int>(p_nf) * nz;
                 // inclusive prefix over the orders of their event counts
                 int einc = lane < H ? cnt : 0;
 #pragma unroll
@@ -251,7 +268,6 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     hdr[b].fa[lane] = p_fa;
                     hdr[b].nf[lane] = static_cast<int>(p_nf);
                     hdr[b].mg[lane] = p_nf > 0 ? (0x100000000ull / p_nf) + 1ull : 0ull;
-                    hdr[b].soff[lane] = p_sinc - scnt;
                     hdr[b].ev[lane + 1] = einc;
                 }
                 if (lane == 0) {
@@ -259,9 +275,16 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                     hdr[b].c0 = p_c0;
                     hdr[b].ev[0] = 0;
                 }
-                // dependencies: poll (bounded) the flags that were still clear when prepared; the
-                // bulk copies then read through the async proxy what other CTAs stored through the
-                // generic proxy, after the flags were acquired
+                // the plane tile does not depend on other bands: its copy starts at once and the
+                // dependency wait below overlaps it
+                unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[b], static_cast<uint32_t>(s.box_bytes));
+                    tensor_g2s_2d(buf, &tmap, p_c0 - kSweepHalo, s.r_lo, &full[b], pol_plane);
+                    pend |= 1u << b;
+                    last_use[b] = u;
+                }
+                // dependencies: poll (bounded) the flags that were still clear when prepared
                 bool unmet = false;
                 if (p_dep >= 0 && p_flag == 0u) {
                     const unsigned long long t0 = global_ns();
@@ -274,29 +297,17 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 // a band whose dependencies were not met would read chain state that was never
                 // written (its drift could point outside the staged tile): the CTA stops instead,
                 // handing the compute warps the end marker
-                if (__any_sync(0xffffffffu, unmet)) {
-                    if (lane == 0) {
-                        s_dead = 1;
-                        hdr[b].task = total;
-                        mbar_arrive(&full[b]);
-                    }
-                    __syncwarp();
-                    break;
+                const bool stop = __any_sync(0xffffffffu, unmet);
+                if (stop && lane == 0) {
+                    s_dead = 1;
+                    hdr[b].task = total;
                 }
+                // the second arrival follows every lane's acquire of its flag (warp barrier), so
+                // the compute warps, which wait for it, see the state those bands stored
                 __syncwarp();
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[b], static_cast<uint32_t>(s.box_bytes + 16 * p_states));
-                    tensor_g2s_2d(buf, &tmap, p_c0 - kSweepHalo, s.r_lo, &full[b], pol_plane);
-                    pend |= 1u << b;
-                    last_use[b] = u;
-                }
+                if (lane == 0) mbar_arrive(&full[b]);
                 __syncwarp();
-                if (lane > 0 && lane < H && p_nf > 0)
-                    bulk_g2s(buf + s.tile_bytes + 16 * static_cast<size_t>(p_sinc - scnt),
-                             s.state + static_cast<long long>(p_fa - f_s) * nz, static_cast<uint32_t>(16 * cnt),
-                             &full[b]);
+                if (stop) break;
             }
             // the next task: its ticket was claimed one task ago
             long long tn = __shfl_sync(0xffffffffu, t_next, 0);
@@ -346,6 +357,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         // its buffer to the control warp and hands the band to the publisher.
         const int ctid = tid - 64;
         const unsigned NW = static_cast<unsigned>(NC >> 5);
+        const uint64_t pol_state = l2_policy_evict_last();
         const int P = s.Wb + 2 * kSweepHalo;
         int rot = 0;   // events of the bands so far, mod NC (the bands' events form one round-robin)
         for (long long k = 0;; ++k) {
@@ -390,7 +402,6 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 jb = static_cast<int>(t - s.n_prefix);
                 const unsigned char *buf = dyn + static_cast<size_t>(b) * s.buf_bytes;
                 const T *tile = reinterpret_cast<const T *>(buf);
-                const int4 *sst = reinterpret_cast<const int4 *>(buf + s.tile_bytes);
                 const int col0 = static_cast<int>(hd.c0 - kSweepHalo);   // plane column of tile column 0
                 // the band's events of every order as one index space e in [0, ev[H]): order h holds
                 // [ev[h-1], ev[h]), within it event i is chain (fa + i % nf, z_lo + i / nf).  Every
@@ -398,52 +409,72 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 // order h + 1 at h f + f >= h f + Wb: a later band), so the orders need no barrier
                 // between them.  The events of successive bands continue one round-robin over the
                 // compute threads, so no thread idles at the end of a band.  A thread's events
-                // increase, so its order h only moves up.
+                // increase, so its order h only moves up.  The state of a thread's next event is
+                // loaded (from L2) while it computes the current one.
                 const int E = hd.ev[H];
                 int e = ctid - rot;
                 if (e < 0) e += NC;
                 rot = (rot + E) % NC;
-                int h = 0, e_hi = 0, nf = 0, fa = 0, so = 0, zrow = 0;
+                int h = 0, e_lo = 0, e_hi = 0, nf = 0, fa = 0;
                 unsigned long long mg = 0ull;
-                float rsh = 0.f, mursh = 0.f;
-                for (; e < E; e += NC) {
-                    if (e >= e_hi) {
+                // event ee -> order hh, chain fh, row index zh (z - z_lo)
+                auto decode = [&](int ee, int &hh, int &fh, int &zh) {
+                    if (ee >= e_hi) {
                         do {
                             ++h;
+                            e_lo = e_hi;
                             e_hi = hd.ev[h];
-                        } while (e >= e_hi);
+                        } while (ee >= e_hi);
                         nf = hd.nf[h - 1];
                         fa = static_cast<int>(hd.fa[h - 1]);
-                        so = hd.soff[h - 1];
                         mg = hd.mg[h - 1];
-                        rsh = rs[h - 1];
-                        mursh = murs[h - 1];
-                        zrow = static_cast<int>(a.z0_row) + h * static_cast<int>(a.z_lo) - 1 - s.r_lo;
                     }
-                    const unsigned i = static_cast<unsigned>(e - hd.ev[h - 1]);
-                    const int zi = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
-                    const int fi = static_cast<int>(i) - zi * nf;
-                    const int f = fa + fi;
-                    Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
-                    if (h > 1) ch = unpack_state(sst[so + fi * nz + zi]);
-                    const int cf = h * f + ch.df;
-                    const int cr = zrow + h * zi + ch.dz;   // staged row of the neighbourhood's top row
-                    const T *p0 = tile + cr * P + (cf - 1 - col0);
-                    float v9[9];
+                    const unsigned i = static_cast<unsigned>(ee - e_lo);
+                    zh = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
+                    fh = fa + (static_cast<int>(i) - zh * nf);
+                    hh = h;
+                };
+                auto state_at = [&](int fh, int zh) { return s.state + static_cast<long long>(zh) * s.nfs + (fh - s.f_s); };
+                if (e < E) {
+                    int hc, fc, zc;
+                    decode(e, hc, fc, zc);
+                    int4 sc = hc > 1 ? ld_state(state_at(fc, zc), pol_state) : make_int4(0, 0, 0, 0);
+                    for (;;) {
+                        const int en = e + NC;
+                        int hn = 0, fn = 0, zn = 0;
+                        int4 sn = make_int4(0, 0, 0, 0);
+                        if (en < E) {
+                            decode(en, hn, fn, zn);
+                            if (hn > 1) sn = ld_state(state_at(fn, zn), pol_state);
+                        }
+                        Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
+                        if (hc > 1) ch = unpack_state(sc);
+                        const int zrow = static_cast<int>(a.z0_row) + hc * static_cast<int>(a.z_lo) - 1 - s.r_lo;
+                        const int cf = hc * fc + ch.df;
+                        const int cr = zrow + hc * zc + ch.dz;   // staged row of the neighbourhood's top row
+                        const T *p0 = tile + cr * P + (cf - 1 - col0);
+                        float v9[9];
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
+                        for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
-                    chain2d_step(ch, h, v9, rsh, mursh);
-                    if (h == H) {
-                        const long long o = static_cast<long long>(zi) * a.nff + (f - a.f_lo);
-                        a.g.snr[o] = ch.best;
-                        a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
-                        if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
-                        const unsigned long long kx = argmax_key(ch.best, o);
-                        key = kx > key ? kx : key;
-                    } else {
-                        __stcg(s.state + static_cast<long long>(f - s.f_s) * nz + zi, pack_state(ch));
+                            for (int q = 0; q < 3; ++q) v9[3 * r + q] = sm_ld<T>(p0 + r * P, q);
+                        chain2d_step(ch, hc, v9, rs[hc - 1], murs[hc - 1]);
+                        if (hc == H) {
+                            const long long o = static_cast<long long>(zc) * a.nff + (fc - a.f_lo);
+                            a.g.snr[o] = ch.best;
+                            a.g.best_h[o] = static_cast<uint8_t>(ch.bh);
+                            if (a.g.path) static_cast<uint32_t *>(a.g.path)[o] = ch.bits;
+                            const unsigned long long kx = argmax_key(ch.best, o);
+                            key = kx > key ? kx : key;
+                        } else {
+                            st_state(state_at(fc, zc), pack_state(ch), pol_state);
+                        }
+                        if (en >= E) break;
+                        e = en;
+                        hc = hn;
+                        fc = fn;
+                        zc = zn;
+                        sc = sn;
                     }
                 }
             }

@@ -8,7 +8,7 @@
 // [j Wb, j Wb + Wb).  A CTA stages the band's columns of the rows the domain can reach (plus a
 // halo of kSweepHalo columns on each side, >= H) in shared memory with one 2D bulk tensor copy,
 // and runs all of the band's events from there; between orders a chain's state (sum, running
-// maximum, path, drift, best order) waits in global memory.  Order h - 1 of a chain f >= Wb lies
+// maximum, path, drift, best order) waits in global memory (L2), read and written there directly.  Order h - 1 of a chain f >= Wb lies
 // in an earlier band (its anchor is h f - f), so a band depends only on earlier bands -- for each
 // order on at most two of them: CTAs take bands in order from a ticket counter and wait (bounded)
 // on the done flags of the bands holding the previous orders of their chains.  Chains with f < f_s stay out of the sweep and run whole in
@@ -35,11 +35,11 @@ struct Sweep2DArgs {
     int32_t Wb;           // anchor columns per band (multiple of 16)
     int32_t r_lo, nr;     // staged rows [r_lo, r_lo + nr)
     int32_t box_bytes;    // bytes of one staged tile, nr x (Wb + 2 kSweepHalo) elements
-    int32_t tile_bytes;   // box_bytes rounded up to 128: offset of the state segments in a buffer
-    int32_t buf_bytes;    // tile_bytes + the largest state of a band, rounded up to 128
+    int32_t buf_bytes;    // box_bytes rounded up to 128: one buffer
     int32_t nbuf;         // buffers, 2..kSweepMaxStages
-    int4 *state;          // [f - f_s][z - z_lo] chain state between orders (f-major: the chains of
-                          // one order of a band, all z, are one contiguous segment)
+    int64_t nfs;          // chains in the sweep, f_hi + 1 - f_s: the row stride of `state`
+    int4 *state;          // [z - z_lo][f - f_s] chain state between orders (z-major: the chains of
+                          // adjacent f that adjacent compute threads run are adjacent)
     unsigned *sync;       // [0] ticket counter, [1] unused, [2 + j] band j done
 };
 

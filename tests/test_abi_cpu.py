@@ -232,7 +232,8 @@ def test_tuning_2d_block_order(hs):
 def test_tuning_2d_sweep(hs):
     """The column sweep (kernel 2): its workspace holds 16 bytes of chain state per sweep chain
     (f >= 64 x 16, the narrowest band) plus one flag per band; it takes 256, 512 or 1024 threads,
-    band widths that are multiples of 16 columns whose buffers fit in shared memory, 2..4 stages;
+    band widths that are multiples of 16 columns (at most 240) whose buffers fit in shared memory,
+    2..4 stages;
     it is refused for checked plans and for rows whose byte stride is not a multiple of 16."""
     n_freq, n_rows, z0, H = 1 << 21, 201, 100, 8
     p = hs.Plan(H, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=n_rows, z0_row=z0, flags=hs.FLAG_NO_DEVICE)
@@ -241,12 +242,17 @@ def test_tuning_2d_sweep(hs):
     nbands = H * f_hi // 16 - f_s // 16 + 1
     assert p.workspace_bytes == nz * (f_hi - f_s + 1) * 16 + (4 * (2 + nbands) + 255) // 256 * 256
     assert p.tuning.kernel == 1                       # the sweep is opt-in
+    # a buffer holds the band's tile, 193 staged rows x (Wb + 16) columns: 2 x 128-column bands fit
+    # in 227 KiB of shared memory, 3 x 64 and 4 x 48 too
     for ok in (dict(kernel=2, threads=512), dict(kernel=2, threads=256, stage_kb=2, stages=3),
-               dict(kernel=2, threads=1024, stage_kb=4, ctas_per_sm=1), dict(kernel=2, threads=512, stage_kb=1, stages=4)):
+               dict(kernel=2, threads=1024, stage_kb=4, ctas_per_sm=1), dict(kernel=2, threads=512, stage_kb=1, stages=4),
+               dict(kernel=2, threads=512, stage_kb=8), dict(kernel=2, threads=512, stage_kb=4, stages=3),
+               dict(kernel=2, threads=512, stage_kb=3, stages=4)):
         p.tuning = ok
         assert p.tuning.kernel == 2
     for bad in (dict(kernel=2, threads=128), dict(kernel=2, threads=512, stages=1), dict(kernel=2, threads=512, stages=5),
-                dict(kernel=2, threads=512, stage_kb=6), dict(kernel=2, threads=512, stage_kb=2, stages=4),
+                dict(kernel=2, threads=512, stage_kb=10), dict(kernel=2, threads=512, stage_kb=4, stages=4),
+                dict(kernel=2, threads=512, stage_kb=16),
                 dict(kernel=2, threads=512, dynamic=1), dict(kernel=1, threads=256, stages=2)):
         with pytest.raises(hs.HSError):
             p.tuning = bad
