@@ -13,10 +13,11 @@ DEV = torch.device("cuda", 0)
 # ---------------------------------------------------------------------------------------------
 # 2D greedy
 # ---------------------------------------------------------------------------------------------
-def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0, tuning=None):
+def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0, tuning=None, default_kernel=None):
     """dtype 1 / 2: the plane is rounded to FP16 / BF16 on the host (round to nearest even) and
     the oracle runs on the rounded values, which FP32 holds exactly.  ``order`` picks kernel 0 or
-    1; ``tuning`` sets any launch shape (the column sweep: kernel 2)."""
+    1; ``tuning`` sets any launch shape (the column sweep: kernel 2); ``default_kernel``: the
+    kernel the plan's default launch shape must name."""
     n_rows, n_freq = pl.shape
     if dtype:
         t = torch.from_numpy(pl).to({1: torch.float16, 2: torch.bfloat16}[dtype])
@@ -30,6 +31,8 @@ def run_2d(hs, o, pl, z0, H, flags=0, mean1=2.0, order=None, dtype=0, tuning=Non
     if tuning is not None:
         plan.tuning = tuning
         assert plan.tuning.kernel == tuning["kernel"]
+    if default_kernel is not None:
+        assert plan.tuning.kernel == default_kernel
     assert plan.domain == o.domain_2d(n_freq, n_rows, z0, H)
     mu, sg = hs.norm_exponential(2, 2, H, True, mean1)
     ng = (torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV))
@@ -80,15 +83,19 @@ def test_2d_integer_ties_bf16(hs, oracle_lib):
 
 
 def test_2d_full_size(hs, oracle_lib):
-    """f-fdot plane 201 x 2^21, H = 8, chi-square(2) noise + 8 drifting tracks."""
+    """f-fdot plane 201 x 2^21, H = 8, chi-square(2) noise + 8 drifting tracks: kernels 0 and 1,
+    the column sweep in its default launch (the FP32 default for a plane this size) and at 512
+    threads, and the FP16 plane (kernel 1 by default)."""
     tracks = synth.random_tracks(8, synth.PLANE_N_FREQ, synth.SEED_BASE + 4 + 1000)
     pl = synth.plane(synth.PLANE_N_FREQ, synth.PLANE_N_ROWS, synth.PLANE_Z0_ROW, synth.SEED_BASE + 4, tracks)
     for order in (0, 1):
         near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, order=order)
         assert near <= 20
+    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, default_kernel=2)
+    assert near <= 20
     near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, tuning=dict(kernel=2, threads=512))
     assert near <= 20
-    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, dtype=1)
+    near = run_2d(hs, oracle_lib, pl, synth.PLANE_Z0_ROW, 8, dtype=1, default_kernel=1)
     assert near <= 20
 
 

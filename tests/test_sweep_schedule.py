@@ -33,6 +33,7 @@ def staged_rows(z0, H, z_lo, z_hi, n_rows):
 
 
 @pytest.mark.parametrize("n_freq,n_rows,z0,H,Wb", [(1 << 17, 201, 100, 8, 64), (1 << 17, 201, 100, 8, 96),
+                                                   (1 << 17, 201, 100, 8, 112), (1 << 17, 201, 100, 8, 128),
                                                    (40000, 61, 30, 4, 16), (65536, 23, 11, 3, 32),
                                                    (2404, 9, 4, 2, 16), (33000, 201, 150, 6, 64),
                                                    (100000, 9, 4, 1, 64)])
