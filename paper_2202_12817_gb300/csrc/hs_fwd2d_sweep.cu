@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 // order h + 1 at h f + f >= h f + Wb: a later band), so the orders need no barrier
                 // between them.  The events of successive bands continue one round-robin over the
                 // compute threads, so no thread idles at the end of a band.  A thread's events
-                // increase, so its order h only moves up.  The state of a thread's next event is
-                // loaded (from L2) while it computes the current one.
+                // increase, so its order h only moves up.  The states of a thread's next two events
+                // are loaded (from L2) while it computes the current one.
                 const int E = hd.ev[H];
                 int e = ctid - rot;
                 if (e < 0) e += NC;
@@ -436,16 +436,21 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 };
                 auto state_at = [&](int fh, int zh) { return s.state + static_cast<long long>(zh) * s.nfs + (fh - s.f_s); };
                 if (e < E) {
-                    int hc, fc, zc;
+                    int hc, fc, zc, hn = 0, fn = 0, zn = 0;
                     decode(e, hc, fc, zc);
                     int4 sc = hc > 1 ? ld_state(state_at(fc, zc), pol_state) : make_int4(0, 0, 0, 0);
+                    int4 sn = make_int4(0, 0, 0, 0);
+                    if (e + NC < E) {
+                        decode(e + NC, hn, fn, zn);
+                        if (hn > 1) sn = ld_state(state_at(fn, zn), pol_state);
+                    }
                     for (;;) {
-                        const int en = e + NC;
-                        int hn = 0, fn = 0, zn = 0;
-                        int4 sn = make_int4(0, 0, 0, 0);
-                        if (en < E) {
-                            decode(en, hn, fn, zn);
-                            if (hn > 1) sn = ld_state(state_at(fn, zn), pol_state);
+                        const int e2 = e + 2 * NC;
+                        int h2 = 0, f2 = 0, z2 = 0;
+                        int4 s2 = make_int4(0, 0, 0, 0);
+                        if (e2 < E) {
+                            decode(e2, h2, f2, z2);
+                            if (h2 > 1) s2 = ld_state(state_at(f2, z2), pol_state);
                         }
                         Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
                         if (hc > 1) ch = unpack_state(sc);
@@ -469,12 +474,16 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                         } else {
                             st_state(state_at(fc, zc), pack_state(ch), pol_state);
                         }
-                        if (en >= E) break;
-                        e = en;
+                        if (e + NC >= E) break;
+                        e += NC;
                         hc = hn;
                         fc = fn;
                         zc = zn;
                         sc = sn;
+                        hn = h2;
+                        fn = f2;
+                        zn = z2;
+                        sn = s2;
                     }
                 }
             }

@@ -241,7 +241,7 @@ def test_tuning_2d_sweep(hs):
     nz, f_s = z_hi - z_lo + 1, 64 * 16
     nbands = H * f_hi // 16 - f_s // 16 + 1
     assert p.workspace_bytes == nz * (f_hi - f_s + 1) * 16 + (4 * (2 + nbands) + 255) // 256 * 256
-    assert p.tuning.kernel == 1                       # the sweep is opt-in
+    assert p.tuning.kernel == 1                       # without a device (no L2 size) the default is kernel 1
     # a buffer holds the band's tile, 193 staged rows x (Wb + 16) columns: 2 x 128-column bands fit
     # in 227 KiB of shared memory, 3 x 64 and 4 x 48 too
     for ok in (dict(kernel=2, threads=512), dict(kernel=2, threads=256, stage_kb=2, stages=3),
