@@ -82,6 +82,7 @@ struct hs_plan_s {
     int path_bytes = 0;
     std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
     std::vector<int64_t> nf_main, tail_tile_start;   // full-harmonic fundamentals; truncated-tail tiles
+    bool equal_lengths = false;   // 1D: every spectrum has one length (so one tile count)
     int64_t total_fund = 0, extent = 0, max_len = 0;
     int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
     hs_tuning tun{1, 256, 1, 0, 0, 0, 0, 0, 0};
@@ -697,6 +698,7 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.tile_start = p->d_tile_start;
     a.in_len = p->d_in_len;
     a.B = static_cast<int32_t>(p->d.num_spectra);
+    a.equal_tiles = p->equal_lengths ? 1 : 0;
     a.H = p->d.H;
     a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;
     a.per_spectrum_norm = (p->d.flags & HS_FLAG_PER_SPECTRUM_NORM) ? 1 : 0;
@@ -1195,6 +1197,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
                 if (p->len[s] != p->len[0]) { delete p; return HS_ERR_INVALID_ARG; }
         p->total_fund = p->fund_off[B];
         p->path_bytes = d.H <= 8 ? 1 : (d.H <= 16 ? 2 : 4);
+        p->equal_lengths = std::all_of(p->len.begin(), p->len.end(), [&](int64_t n) { return n == p->len[0]; });
     } else if (d.dims == 2) {
         if (d.H < 1 || d.H > kMaxH2D || d.forms != HS_FORM_GREEDY) { delete p; return HS_ERR_INVALID_ARG; }
         if (d.num_spectra != 1) { delete p; return HS_ERR_INVALID_ARG; }

@@ -135,9 +135,19 @@ __device__ __forceinline__ void prefetch_next_spectrum(const Fwd1DArgs &a, int s
     }
 }
 
-// spectrum owning a tile: largest s with tile_start[s] <= t
-__device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t)
+// spectrum owning a tile: largest s with tile_start[s] <= t.  With equal tile counts (a plan whose
+// spectra all have one length) it is (t - tile_start[0]) / count: two loads instead of a dependent
+// chain of log2 B.
+__device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t, int equal)
 {
+    if (B == 1) return 0;
+    if (equal) {
+        // tile counts below 2^31 (the host keeps launches within that), so 32-bit divisions
+        const int64_t a0 = __ldg(tile_start), aB = __ldg(tile_start + B);
+        const unsigned per = static_cast<unsigned>(aB - a0) / static_cast<unsigned>(B);
+        const unsigned g = per > 0 ? static_cast<unsigned>(t - a0) / per : 0u;
+        return g < static_cast<unsigned>(B) ? static_cast<int>(g) : B - 1;
+    }
     int lo = 0, hi = B - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
         tile = s_tile;
     }
     while (tile < a.total_tiles) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
     const int H = a.H;
     int loaded_spec = -1;
     for (int64_t tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();

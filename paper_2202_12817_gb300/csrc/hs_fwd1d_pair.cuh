@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
         tile = s_tile;
     }
     while (tile < a.total_tiles) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();

@@ -43,6 +43,7 @@ struct Fwd1DArgs {
     const int64_t *tile_start;     // [B+1] prefix of tiles per spectrum
     const int64_t *in_len;         // [B] N_s (for checked mode)
     int32_t B;
+    int32_t equal_tiles;           // 1: every spectrum has the same tile count (one length for all)
     int32_t H;
     int32_t mitigation;
     int32_t per_spectrum_norm;
