@@ -698,7 +698,14 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.tile_start = p->d_tile_start;
     a.in_len = p->d_in_len;
     a.B = static_cast<int32_t>(p->d.num_spectra);
-    a.equal_tiles = p->equal_lengths ? 1 : 0;
+    // one tile count for every spectrum: the kernels find a tile's spectrum by a division (below
+    // 2^22 tiles a single-precision estimate is within one of the quotient)
+    if (p->equal_lengths && p->tile_start.back() < (int64_t(1) << 22) && p->tail_tile_start.back() < (int64_t(1) << 22)) {
+        a.tiles_per_spec = static_cast<uint32_t>(p->tile_start.back() / p->d.num_spectra);
+        a.tail_tiles_per_spec = static_cast<uint32_t>(p->tail_tile_start.back() / p->d.num_spectra);
+        a.inv_tiles_per_spec = a.tiles_per_spec ? 1.0f / static_cast<float>(a.tiles_per_spec) : 0.f;
+        a.inv_tail_tiles_per_spec = a.tail_tiles_per_spec ? 1.0f / static_cast<float>(a.tail_tiles_per_spec) : 0.f;
+    }
     a.H = p->d.H;
     a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;
     a.per_spectrum_norm = (p->d.flags & HS_FLAG_PER_SPECTRUM_NORM) ? 1 : 0;

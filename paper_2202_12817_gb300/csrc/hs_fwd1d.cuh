@@ -135,17 +135,19 @@ __device__ __forceinline__ void prefetch_next_spectrum(const Fwd1DArgs &a, int s
     }
 }
 
-// spectrum owning a tile: largest s with tile_start[s] <= t.  With equal tile counts (a plan whose
-// spectra all have one length) it is (t - tile_start[0]) / count: two loads instead of a dependent
-// chain of log2 B.
-__device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t, int equal)
+// spectrum owning a tile: largest s with tile_start[s] <= t.  `per` > 0: every spectrum has that
+// many tiles (a plan whose spectra all have one length; the host passes it below 2^22 tiles, with
+// inv = fl(1/per)), so it is x / per for x = t - tile_start[0] (tile_start[0] is 0, or minus a
+// chunk's first tile): a single-precision estimate, within one of x / per there, and an exact
+// integer correction.  Otherwise a binary search, a chain of log2 B dependent loads.
+__device__ __forceinline__ int tile_spectrum(const int64_t *tile_start, int B, int64_t t, unsigned per, float inv)
 {
     if (B == 1) return 0;
-    if (equal) {
-        // tile counts below 2^31 (the host keeps launches within that), so 32-bit divisions
-        const int64_t a0 = __ldg(tile_start), aB = __ldg(tile_start + B);
-        const unsigned per = static_cast<unsigned>(aB - a0) / static_cast<unsigned>(B);
-        const unsigned g = per > 0 ? static_cast<unsigned>(t - a0) / per : 0u;
+    if (per > 0) {
+        const unsigned x = static_cast<unsigned>(t - __ldg(tile_start));
+        unsigned g = __float2uint_rz(__uint2float_rn(x) * inv);
+        if (g * per > x) --g;
+        else if ((g + 1) * per <= x) ++g;
         return g < static_cast<unsigned>(B) ? static_cast<int>(g) : B - 1;
     }
     int lo = 0, hi = B - 1;
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(256) k_fwd1d(const Fwd1DArgs a)
         tile = s_tile;
     }
     while (tile < a.total_tiles) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.tiles_per_spec, a.inv_tiles_per_spec);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(256) k_fwd1d_x2(const Fwd1DArgs a)
     const int H = a.H;
     int loaded_spec = -1;
     for (int64_t tile = blockIdx.x; tile < a.total_tiles; tile += gridDim.x) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.tiles_per_spec, a.inv_tiles_per_spec);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(256, 8) k_fwd1d_pair(const Fwd1DArgs a)
         tile = s_tile;
     }
     while (tile < a.total_tiles) {
-        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
+        // the fused one-chain kernel (kernel 6, the default for one FP32 spectrum) keeps the search:
+        // the division path would push it past its 32 registers
+        constexpr bool kSearchOnly = kBoth && CH == 1;
+        const int s = tile_spectrum(a.tile_start, a.B, tile, kSearchOnly ? 0u : a.tiles_per_spec, a.inv_tiles_per_spec);
         prefetch_next_spectrum(a, s, tile);
         if (s != loaded_spec) {
             if (loaded_spec >= 0) __syncthreads();

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
     constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
     const int H = a.H;
     const int64_t tile = a.tail_tiles - 1 - static_cast<int64_t>(blockIdx.x);
-    const int s = tile_spectrum(a.tail_tile_start, a.B, tile, a.equal_tiles);
+    const int s = tile_spectrum(a.tail_tile_start, a.B, tile, a.tail_tiles_per_spec, a.inv_tail_tiles_per_spec);
     const int64_t t0 = __ldg(a.tail_tile_start + s), t1 = __ldg(a.tail_tile_start + s + 1);
     const int64_t fbase = __ldg(a.fund_off + s);
     const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(640) k_fwd1d_win(const Fwd1DArgs a, const WinP
             }
             if (s_abort) { ok = false; break; }
             const int64_t tile = blockIdx.x + k * gridDim.x;
-            const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
+            const int s = tile_spectrum(a.tile_start, a.B, tile, a.tiles_per_spec, a.inv_tiles_per_spec);
             const int64_t nf = __ldg(a.nf_main + s);
             const int64_t n0 = (tile - __ldg(a.tile_start + s)) * Tn;
             const int64_t n_last = (n0 + Tn < nf ? n0 + Tn : nf) - 1;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(640) k_fwd1d_win(const Fwd1DArgs a, const WinP
     int loaded_spec = -1;
     for (int64_t k = 0; k < my_tiles; ++k) {
         const int64_t tile = blockIdx.x + k * gridDim.x;
-        const int s = tile_spectrum(a.tile_start, a.B, tile, a.equal_tiles);
+        const int s = tile_spectrum(a.tile_start, a.B, tile, a.tiles_per_spec, a.inv_tiles_per_spec);
         if (s != loaded_spec) {
             consumer_sync(Tn);
             const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;

@@ -43,7 +43,11 @@ struct Fwd1DArgs {
     const int64_t *tile_start;     // [B+1] prefix of tiles per spectrum
     const int64_t *in_len;         // [B] N_s (for checked mode)
     int32_t B;
-    int32_t equal_tiles;           // 1: every spectrum has the same tile count (one length for all)
+    uint32_t tiles_per_spec;       // > 0: every spectrum has this many main-pass tiles (one length for
+                                   // all, fewer than 2^22 tiles in all)
+    uint32_t tail_tiles_per_spec;  // > 0: likewise for the truncated-tail tiles
+    float inv_tiles_per_spec;      // fl(1 / tiles_per_spec), fl(1 / tail_tiles_per_spec)
+    float inv_tail_tiles_per_spec;
     int32_t H;
     int32_t mitigation;
     int32_t per_spectrum_norm;
