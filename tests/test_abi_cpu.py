@@ -268,6 +268,23 @@ def test_tuning_2d_sweep(hs):
         q.close()
 
 
+def test_sweep_default_band_width_narrows_to_the_plane(hs):
+    """stage_kb = 0 takes 112-column bands for FP32 where the plane has chains beyond the 64-band-width
+    register prefix, else the widest narrower multiple of 16 that has some (33000 x 201 rows, H = 6:
+    f_hi = 5498, so 112 (f_s = 7168) is too wide but 80 (f_s = 5120) is not); nothing fits a plane
+    whose chains all lie in the prefix of the narrowest band."""
+    p = plan(hs, H=6, forms=hs.GREEDY, dims=2, n_freq=33000, n_rows=201, z0_row=150)
+    assert p.domain[1] == 5498
+    p.tuning = dict(kernel=2, threads=512)
+    assert p.tuning.kernel == 2 and p.tuning.stage_kb == 0
+    with pytest.raises(hs.HSError):
+        p.tuning = dict(kernel=2, threads=512, stage_kb=7)       # 112 columns given explicitly
+    p.tuning = dict(kernel=2, threads=512, stage_kb=5)           # 80 columns: f_s = 5120 <= 5498
+    q = plan(hs, H=6, forms=hs.GREEDY, dims=2, n_freq=6000, n_rows=201, z0_row=150)
+    with pytest.raises(hs.HSError):                               # f_hi = 998 < 64 x 16
+        q.tuning = dict(kernel=2, threads=512)
+
+
 def test_selftest_timeout_needs_device(hs):
     p = plan(hs, H=8, forms=hs.GREEDY, lengths=[1000])
     with pytest.raises(hs.HSError) as e:
