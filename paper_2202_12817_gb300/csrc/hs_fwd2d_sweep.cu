@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
         // its buffer to the control warp and hands the band to the publisher.
         const int ctid = tid - 64;
         const unsigned NW = static_cast<unsigned>(NC >> 5);
-        const uint64_t pol_state = l2_policy_evict_last();
+        // state kept in L2 ahead of the tiles (evict-last), except the last read of a chain's state
+        // (order H reads order H - 1's): evict-first, so no dead state outlives the pass in L2
+        const uint64_t pol_state = l2_policy_evict_last(), pol_dead = l2_policy_evict_first();
         const int P = s.Wb + 2 * kSweepHalo;
         int rot = 0;   // events of the bands so far, mod NC (the bands' events form one round-robin)
         for (long long k = 0;; ++k) {
@@ -438,11 +440,11 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 if (e < E) {
                     int hc, fc, zc, hn = 0, fn = 0, zn = 0;
                     decode(e, hc, fc, zc);
-                    int4 sc = hc > 1 ? ld_state(state_at(fc, zc), pol_state) : make_int4(0, 0, 0, 0);
+                    int4 sc = hc > 1 ? ld_state(state_at(fc, zc), hc == H ? pol_dead : pol_state) : make_int4(0, 0, 0, 0);
                     int4 sn = make_int4(0, 0, 0, 0);
                     if (e + NC < E) {
                         decode(e + NC, hn, fn, zn);
-                        if (hn > 1) sn = ld_state(state_at(fn, zn), pol_state);
+                        if (hn > 1) sn = ld_state(state_at(fn, zn), hn == H ? pol_dead : pol_state);
                     }
                     for (;;) {
                         const int e2 = e + 2 * NC;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                         int4 s2 = make_int4(0, 0, 0, 0);
                         if (e2 < E) {
                             decode(e2, h2, f2, z2);
-                            if (h2 > 1) s2 = ld_state(state_at(f2, z2), pol_state);
+                            if (h2 > 1) s2 = ld_state(state_at(f2, z2), h2 == H ? pol_dead : pol_state);
                         }
                         Chain2D ch{0.f, 0.f, 0u, 0, 0, 1};
                         if (hc > 1) ch = unpack_state(sc);
