@@ -186,6 +186,7 @@ SweepGeom sweep_geom(const hs_plan p, int Wb, int threads, int nbuf = 2, int64_t
     g.band_lo = f_s / Wb;
     g.nbands = H * p->f_hi / Wb - g.band_lo + 1;
     g.n_prefix = ((f_s - p->f_lo) * nz + compute - 1) / compute;
+    if (nz * (p->f_hi - f_s + 1) >= (int64_t(1) << 31)) return g;   // the kernel indexes the state in 32 bits
     g.state_bytes = static_cast<size_t>(nz * (p->f_hi - f_s + 1)) * 16;
     g.sync_bytes = (static_cast<size_t>(2 + g.nbands) * 4 + 255) / 256 * 256;
     g.ok = true;

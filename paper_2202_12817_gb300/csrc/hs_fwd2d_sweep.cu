@@ -124,8 +124,8 @@ struct BandHdr {
     long long fa[kMaxH2D];     // order h = k + 1 holds chains [fa[k], fa[k] + nf[k]), all z
     int nf[kMaxH2D];
     int ev[kMaxH2D + 1];       // events of orders < h: order h's events are [ev[h-1], ev[h])
-    unsigned long long mg[kMaxH2D];  // floor(2^32 / nf) + 1: i / nf = (i mg) >> 32 for the event
-                                     // index i of an order (i nf < 2^32)
+    unsigned mg[kMaxH2D];      // floor(2^32 / nf) + 1 for nf > 1 (0 for nf = 1): i / nf = (i mg) >> 32 for
+                               // the event index i of an order (i nf < 2^32)
 };
 }  // namespace
 
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 if (lane < H) {
                     hdr[b].fa[lane] = p_fa;
                     hdr[b].nf[lane] = static_cast<int>(p_nf);
-                    hdr[b].mg[lane] = p_nf > 0 ? (0x100000000ull / p_nf) + 1ull : 0ull;
+                    hdr[b].mg[lane] = p_nf > 1 ? static_cast<unsigned>(0x100000000ull / p_nf + 1ull) : 0u;
                     hdr[b].ev[lane + 1] = einc;
                 }
                 if (lane == 0) {
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 if (e < 0) e += NC;
                 rot = (rot + E) % NC;
                 int h = 0, e_lo = 0, e_hi = 0, nf = 0, fa = 0;
-                unsigned long long mg = 0ull;
+                unsigned mg = 0u;
                 // event ee -> order hh, chain fh, row index zh (z - z_lo)
                 auto decode = [&](int ee, int &hh, int &fh, int &zh) {
                     if (ee >= e_hi) {
@@ -432,11 +432,15 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                         mg = hd.mg[h - 1];
                     }
                     const unsigned i = static_cast<unsigned>(ee - e_lo);
-                    zh = static_cast<int>((static_cast<unsigned long long>(i) * mg) >> 32);
+                    zh = nf > 1 ? static_cast<int>(__umulhi(i, mg)) : static_cast<int>(i);
                     fh = fa + (static_cast<int>(i) - zh * nf);
                     hh = h;
                 };
-                auto state_at = [&](int fh, int zh) { return s.state + static_cast<long long>(zh) * s.nfs + (fh - s.f_s); };
+                // state entry of chain (fh, z_lo + zh): fewer than 2^31 entries (the host checks)
+                const unsigned nfs32 = static_cast<unsigned>(s.nfs), fs32 = static_cast<unsigned>(s.f_s);
+                auto state_at = [&](int fh, int zh) {
+                    return s.state + (static_cast<unsigned>(zh) * nfs32 + (static_cast<unsigned>(fh) - fs32));
+                };
                 if (e < E) {
                     int hc, fc, zc, hn = 0, fn = 0, zn = 0;
                     decode(e, hc, fc, zc);
