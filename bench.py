@@ -368,6 +368,16 @@ def roofline(alg_bytes, ms, peak, peak_kind, wl, how, tuning=None):
             "kernel": pk.get("kernel") if fresh else None}
 
 
+def plane_launch_text(t):
+    """What one 2D step launches, from the plan's launch shape."""
+    if t.get("kernel") == 2:
+        return ("column sweep (kernel 2): one persistent CTA of %d threads per SM takes bands of anchor columns, "
+                "each staged once for all orders; chains f < %d band widths run whole in registers first"
+                % (t.get("threads", 0), 64 * max(1, t.get("producers", 0))))
+    return "one thread per (f, z) chain (kernel %d), CTAs over %s fastest" % (
+        t.get("kernel", 0), "z rows" if t.get("kernel") == 1 else "f tiles")
+
+
 def launch_text(t):
     """What one step launches, from the plan's (autotuned) launch shape."""
     if t.get("ctas_per_sm", 0) > 0:
@@ -651,7 +661,7 @@ def wl_plane(args, hs, torch, dev, world, dist):
         "config": {"workload": "2D greedy over an f-fdot plane 201 x 2^21 (%s), H=8, 8 drifting signals"
                                % {hs.F32: "FP32", hs.F16: "FP16", hs.BF16: "BF16"}[dtype],
                    "fundamentals": int(nfund), "H": H, "domain": list(plan.domain), "tuning": plan.tuning.as_dict(),
-                   "l2": "input larger than L2 (no flush)"},
+                   "launch": plane_launch_text(plan.tuning.as_dict()), "l2": "input larger than L2 (no flush)"},
         "roofline": roofline(alg, ms, peak, peak_kind, wl, how, plan.tuning.as_dict()),
         "gpu_launches": steps, "wall_s_timed_region": round(wall, 3),
     }

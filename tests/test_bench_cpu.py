@@ -26,6 +26,13 @@ def test_launch_text_names_the_tuned_shape():
     assert "strided" in bench.launch_text(_tuning(kernel=1, ctas_per_sm=2))
 
 
+def test_plane_launch_text_names_the_kernel():
+    sweep = bench.plane_launch_text(_tuning(kernel=2, threads=1024, producers=5))
+    assert "column sweep" in sweep and "1024 threads" in sweep and "320 band widths" in sweep
+    assert "z rows" in bench.plane_launch_text(_tuning(kernel=1))
+    assert "f tiles" in bench.plane_launch_text(_tuning(kernel=0))
+
+
 def test_traffic_entry_matches_sources_and_shape(tmp_path, monkeypatch):
     h = bench.kernel_hash("long")
     t6, t7 = _tuning(kernel=6, threads=128), _tuning(kernel=7, threads=256, ctas_per_sm=8, dynamic=1)
