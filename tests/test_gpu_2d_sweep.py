@@ -89,9 +89,10 @@ def _outputs(hs, plan, pl_dev, H, fixed=False):
 
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_sweep_equals_kernel1(hs, dtype):
-    """201 x 2^19 plane, H = 8: kernel 2 gives kernel 1's outputs bit for bit, in four launch shapes and in
-    the plan's default (the sweep for this FP32 plane, 421 MB, with chains beyond its 320-band-width prefix)."""
-    n_freq = 1 << 19
+    """201 x 2^18 plane, H = 8: kernel 2 gives kernel 1's outputs bit for bit in four launch shapes; the
+    plan's default for this plane (211 MB, under 8 L2 sizes) is kernel 1 (the sweep's default launch is
+    checked on the full 201 x 2^21 plane in test_gpu_2d_bwd.py)."""
+    n_freq = 1 << 18
     tracks = synth.random_tracks(8, n_freq, 333)
     pl = torch.from_numpy(synth.plane(n_freq, 201, 100, 334, tracks))
     if dtype:
@@ -103,9 +104,8 @@ def test_sweep_equals_kernel1(hs, dtype):
         plan = hs.Plan(8, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=201, z0_row=100, dtype=dtype)
         if t is not None:
             plan.tuning = t
-        else:   # the default: the sweep for an FP32 plane larger than L2, kernel 1 for 16-bit storage
-            assert plan.tuning.kernel == (2 if dtype == 0 else 1)
-            assert plan.tuning.threads == (1024 if dtype == 0 else 256)
+        else:
+            assert plan.tuning.kernel == 1 and plan.tuning.threads == 256
         outs.append(_outputs(hs, plan, pl_dev, 8))
         plan.close()
     for o in outs[1:]:
