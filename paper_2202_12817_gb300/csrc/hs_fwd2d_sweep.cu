@@ -323,10 +323,10 @@ __global__ void __launch_bounds__(kSweepMaxThreads, 1) k_fwd2d_sweep(const __gri
                 }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- publisher: mark finished bands done.  The compute warps push each finished band on
-        // a shared ring; one GPU-scope fence then covers every band pushed so far (their state
-        // stores were ordered before the push by the compute warps' barrier), so a fence per
-        // batch rather than per band sets the flags.
+        // ---- publisher: mark finished bands done.  The last compute warp done with a band pushes
+        // it on a shared ring; one GPU-scope fence then covers every band pushed so far (every
+        // warp's state stores were ordered before the push by the block-scope release / acquire
+        // of the warps' done count), so a fence per batch rather than per band sets the flags.
         if (lane == 0) {
             unsigned tail = 0u;
             bool end = false;
