@@ -120,10 +120,16 @@ def test_unordered_offsets_single_chunk(hs):
     check(hs, plan, layout(plan, xs, 0))
 
 
-def test_plane(hs):
+@pytest.mark.parametrize("tuning", [None, dict(kernel=2, threads=512)])
+def test_plane(hs, tuning):
+    """A plane goes in one copy; then kernel 1 or the column sweep (here at the 16-column band
+    width the plane takes) runs as under hs_run."""
     z0 = 30
     pl = synth.plane(5003, 2 * z0 + 1, z0, 12, synth.random_tracks(3, 5003, 8, f_lo=50, zmax=3))
     plan = hs.Plan(4, hs.GREEDY, dims=2, n_freq=5003, n_rows=2 * z0 + 1, z0_row=z0)
+    if tuning:
+        plan.tuning = tuning
+        assert plan.tuning.kernel == 2
     check(hs, plan, torch.from_numpy(pl).reshape(-1))
 
 
