@@ -120,13 +120,13 @@ def test_unordered_offsets_single_chunk(hs):
     check(hs, plan, layout(plan, xs, 0))
 
 
-@pytest.mark.parametrize("tuning", [None, dict(kernel=2, threads=512)])
-def test_plane(hs, tuning):
+@pytest.mark.parametrize("n_freq,tuning", [(5003, None), (5008, dict(kernel=2, threads=512))])
+def test_plane(hs, n_freq, tuning):
     """A plane goes in one copy; then kernel 1 or the column sweep (here at the 16-column band
-    width the plane takes) runs as under hs_run."""
+    width the plane takes; its rows must be a multiple of 16 bytes) runs as under hs_run."""
     z0 = 30
-    pl = synth.plane(5003, 2 * z0 + 1, z0, 12, synth.random_tracks(3, 5003, 8, f_lo=50, zmax=3))
-    plan = hs.Plan(4, hs.GREEDY, dims=2, n_freq=5003, n_rows=2 * z0 + 1, z0_row=z0)
+    pl = synth.plane(n_freq, 2 * z0 + 1, z0, 12, synth.random_tracks(3, n_freq, 8, f_lo=50, zmax=3))
+    plan = hs.Plan(4, hs.GREEDY, dims=2, n_freq=n_freq, n_rows=2 * z0 + 1, z0_row=z0)
     if tuning:
         plan.tuning = tuning
         assert plan.tuning.kernel == 2
