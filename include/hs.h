@@ -180,8 +180,8 @@ hs_status hs_plan_workspace(hs_plan plan, size_t *bytes);
  * registers before the sweep takes over; 0: 64 band widths); it needs rows whose byte stride is
  * a multiple of 16, at most 256 reachable rows, no HS_FLAG_CHECKED, and the workspace (without
  * one, hs_run and hs_run_fixed_scratch run it as kernel 1, with the same outputs bit for bit).
- * The default is kernel 1, except for FP32 planes of 8 or more times the device's L2 size that
- * the sweep takes: kernel 2 with 1024 threads and producers 5. */
+ * The default is kernel 1, except for FP32 planes of 8 or more times the device's L2 size with
+ * H >= 6 that the sweep takes: kernel 2 with 1024 threads and producers 5. */
 hs_status hs_plan_get_tuning(hs_plan plan, hs_tuning *t);
 hs_status hs_plan_set_tuning(hs_plan plan, const hs_tuning *t);
 

@@ -1259,12 +1259,14 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         // the default launch shape depends on whether the input fits in this device's L2
         p->tun = default_tuning(p);
         compute_tiles(p);
-    } else if (d.dtype == HS_F32 && p->extent * 4 >= 8 * static_cast<int64_t>(p->l2_bytes)) {
-        // an FP32 plane of 8 L2 sizes or more runs the column sweep where it applies: on 201-row
-        // planes, H = 8, it takes 525 us vs 638 us for kernel 1 at 2^21 columns (13 L2 sizes), 294 vs
-        // 302 us at 2^20 and 188 vs 135 us at 2^19 (3.3 L2 sizes, where kernel 1's re-reads still
-        // mostly hit L2) -- 112-column bands, 1024 threads, chains f < 320 band widths in registers
-        // first.  16-bit planes keep kernel 1 (428 us vs 519 us at 2^21: half the bytes make kernel
+    } else if (d.dtype == HS_F32 && d.H >= 6 && p->extent * 4 >= 8 * static_cast<int64_t>(p->l2_bytes)) {
+        // an FP32 plane of 8 L2 sizes or more, summed to 6 orders or more, runs the column sweep where
+        // it applies: on 201-row planes, H = 8, it takes 525 us vs 638 us for kernel 1 at 2^21 columns
+        // (13 L2 sizes), 294 vs 302 us at 2^20 and 188 vs 135 us at 2^19 (3.3 L2 sizes, where kernel
+        // 1's re-reads still mostly hit L2); at 2^21 columns and H = 6 608 vs 615 us, but at H = 4 903
+        // vs 654 us and at H = 2 1379 vs 1293 us (fewer orders re-read less, and the domain holds more
+        // chains) -- 112-column bands, 1024 threads, chains f < 320 band widths in registers first.
+        // 16-bit planes keep kernel 1 (428 us vs 519 us at 2^21, H = 8: half the bytes make kernel
         // 1's re-reads cheaper, while the sweep's cost barely changes).
         const hs_tuning sw{2, 1024, 1, 0, 0, 0, 0, 0, 5};
         const SweepGeom g = sweep_geom(p, sweep_default_wb(d.dtype), sw.threads, 2, kSweepPrefixBands * sw.producers);
