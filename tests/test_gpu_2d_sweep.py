@@ -32,7 +32,7 @@ def test_sweep_longer_prefix(hs, oracle_lib, producers):
     run_2d(hs, oracle_lib, pl, z0, 8, tuning=dict(kernel=2, threads=512, stage_kb=1, producers=producers))
 
 
-@pytest.mark.parametrize("H", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("H", [1, 2, 3, 5, 6, 7, 8])
 def test_sweep_orders(hs, oracle_lib, H):
     z0 = 24
     pl = synth.plane(65536, 2 * z0 + 1, z0, 110 + H, synth.random_tracks(3, 65536, 8, f_lo=50, zmax=2))
