@@ -82,6 +82,7 @@ struct hs_plan_s {
     int path_bytes = 0;
     std::vector<int64_t> len, in_off, nf, fund_off, tile_start;
     std::vector<int64_t> nf_main, tail_tile_start;   // full-harmonic fundamentals; truncated-tail tiles
+    std::vector<int64_t> tail1_tile_start;           // tiles of the tail's one-order fundamentals
     bool equal_lengths = false;   // 1D: every spectrum has one length (so one tile count)
     int64_t total_fund = 0, extent = 0, max_len = 0;
     int64_t f_lo = 0, f_hi = -1, z_lo = 0, z_hi = -1;
@@ -90,7 +91,7 @@ struct hs_plan_s {
     WinPlan wplan{};
     // device tables
     int64_t *d_in_off = nullptr, *d_fund_off = nullptr, *d_tile_start = nullptr, *d_in_len = nullptr;
-    int64_t *d_nf_main = nullptr, *d_tail_tile_start = nullptr;
+    int64_t *d_nf_main = nullptr, *d_tail_tile_start = nullptr, *d_tail1_tile_start = nullptr;
     int *d_err = nullptr;
     // graph replay
     cudaStream_t cap = nullptr;
@@ -322,9 +323,17 @@ void compute_tiles(hs_plan p)
     p->tile_start.assign(B + 1, 0);
     // the main kernels cover the fundamentals with all H orders; the truncated tail has its own tiles
     for (size_t s = 0; s < B; ++s) p->tile_start[s + 1] = p->tile_start[s] + (p->nf_main[s] + T - 1) / T;
+    // the truncated tail in two parts: N_f <= n < min(N - 1, n1), where the orders that fit vary, and
+    // max(n1, N_f) <= n < N - 1, where both forms keep order 1 only (n1 = floor((N - 1) / 2) + 1)
     p->tail_tile_start.assign(B + 1, 0);
-    for (size_t s = 0; s < B; ++s)
-        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (p->nf[s] - p->nf_main[s] + kTailTile - 1) / kTailTile;
+    p->tail1_tile_start.assign(B + 1, 0);
+    for (size_t s = 0; s < B; ++s) {
+        const int64_t n1 = (p->len[s] - 1) / 2 + 1;
+        const int64_t g = std::max<int64_t>(0, std::min(p->nf[s], n1) - p->nf_main[s]);
+        const int64_t o = std::max<int64_t>(0, p->nf[s] - std::max(n1, p->nf_main[s]));
+        p->tail_tile_start[s + 1] = p->tail_tile_start[s] + (g + kTailTile - 1) / kTailTile;
+        p->tail1_tile_start[s + 1] = p->tail1_tile_start[s] + (o + kTail1Tile - 1) / kTail1Tile;
+    }
     make_win_plan(p);
     make_chunks(p);
 }
@@ -462,6 +471,7 @@ void free_plan(hs_plan p)
         cudaFree(p->d_tile_start);
         cudaFree(p->d_nf_main);
         cudaFree(p->d_tail_tile_start);
+        cudaFree(p->d_tail1_tile_start);
         cudaFree(p->d_in_len);
         cudaFree(p->d_err);
         cudaFree(p->d_chunk_tile_start);
@@ -502,12 +512,12 @@ FormArgs to_form_args(const hs_form_io *io)
     return f;
 }
 
-const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
+const void *fwd1d_tail_kernel(int dtype, int forms, int whitening, int one_order)
 {
     switch (dtype) {
-    case HS_F32: return fwd1d_tail_kernel_f32(forms, whitening);
-    case HS_F16: return fwd1d_tail_kernel_f16(forms, whitening);
-    case HS_BF16: return fwd1d_tail_kernel_bf16(forms, whitening);
+    case HS_F32: return fwd1d_tail_kernel_f32(forms, whitening, one_order);
+    case HS_F16: return fwd1d_tail_kernel_f16(forms, whitening, one_order);
+    case HS_BF16: return fwd1d_tail_kernel_bf16(forms, whitening, one_order);
     }
     return nullptr;
 }
@@ -536,20 +546,29 @@ hs_status launch_fwd(const void *fn, dim3 grid, dim3 block, void **args, size_t 
     return HS_OK;
 }
 
-// The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel.
+// The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel --
+// those below n1 = floor((N - 1) / 2) + 1 first, then the one-order rest.
 hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st, bool prewhitened = false)
 {
-    if (!(p->d.flags & HS_FLAG_TRUNCATE_TAIL) || main_args.tail_tiles <= 0) return HS_OK;
-    if (main_args.tail_tiles > 0x7fffffff) return HS_ERR_UNSUPPORTED;
+    if (!(p->d.flags & HS_FLAG_TRUNCATE_TAIL)) return HS_OK;
+    if (main_args.tail_tiles > 0x7fffffff || main_args.tail1_tiles > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     // on the pre-whitened copy the tail reads plain FP32
-    const void *fn = prewhitened ? fwd1d_tail_kernel(HS_F32, p->d.forms & 3, 0)
-                                 : fwd1d_tail_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0);
-    if (!fn) return HS_ERR_UNSUPPORTED;
+    const int dt = prewhitened ? HS_F32 : p->d.dtype;
+    const int wh = (!prewhitened && (p->d.flags & HS_FLAG_WHITENING)) ? 1 : 0;
     Fwd1DArgs a = main_args;
     a.tile_counter = nullptr;
     a.pf_chunk = 0;
     void *args[] = {&a};
-    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail_tiles)), dim3(kTailThreads), args, 0, st));
+    if (a.tail_tiles > 0) {
+        const void *fn = fwd1d_tail_kernel(dt, p->d.forms & 3, wh, 0);
+        if (!fn) return HS_ERR_UNSUPPORTED;
+        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail_tiles)), dim3(kTailThreads), args, 0, st));
+    }
+    if (a.tail1_tiles > 0) {
+        const void *fn = fwd1d_tail_kernel(dt, p->d.forms & 3, wh, 1);
+        if (!fn) return HS_ERR_UNSUPPORTED;
+        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail1_tiles)), dim3(kTailThreads), args, 0, st));
+    }
     return HS_OK;
 }
 
@@ -696,16 +715,21 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
     a.nf_main = p->d_nf_main;
     a.tail_tile_start = p->d_tail_tile_start;
     a.tail_tiles = p->tail_tile_start.empty() ? 0 : p->tail_tile_start.back();
+    a.tail1_tile_start = p->d_tail1_tile_start;
+    a.tail1_tiles = p->tail1_tile_start.empty() ? 0 : p->tail1_tile_start.back();
     a.tile_start = p->d_tile_start;
     a.in_len = p->d_in_len;
     a.B = static_cast<int32_t>(p->d.num_spectra);
     // one tile count for every spectrum: the kernels find a tile's spectrum by a division (below
     // 2^22 tiles a single-precision estimate is within one of the quotient)
-    if (p->equal_lengths && p->tile_start.back() < (int64_t(1) << 22) && p->tail_tile_start.back() < (int64_t(1) << 22)) {
+    if (p->equal_lengths && p->tile_start.back() < (int64_t(1) << 22) && p->tail_tile_start.back() < (int64_t(1) << 22) &&
+        p->tail1_tile_start.back() < (int64_t(1) << 22)) {
         a.tiles_per_spec = static_cast<uint32_t>(p->tile_start.back() / p->d.num_spectra);
         a.tail_tiles_per_spec = static_cast<uint32_t>(p->tail_tile_start.back() / p->d.num_spectra);
+        a.tail1_tiles_per_spec = static_cast<uint32_t>(p->tail1_tile_start.back() / p->d.num_spectra);
         a.inv_tiles_per_spec = a.tiles_per_spec ? 1.0f / static_cast<float>(a.tiles_per_spec) : 0.f;
         a.inv_tail_tiles_per_spec = a.tail_tiles_per_spec ? 1.0f / static_cast<float>(a.tail_tiles_per_spec) : 0.f;
+        a.inv_tail1_tiles_per_spec = a.tail1_tiles_per_spec ? 1.0f / static_cast<float>(a.tail1_tiles_per_spec) : 0.f;
     }
     a.H = p->d.H;
     a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;
@@ -1277,6 +1301,7 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         !cuda_ok(cudaMalloc(&p->d_fund_off, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_tile_start, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_tail_tile_start, sizeof(int64_t) * B1)) ||
+        !cuda_ok(cudaMalloc(&p->d_tail1_tile_start, sizeof(int64_t) * B1)) ||
         !cuda_ok(cudaMalloc(&p->d_nf_main, sizeof(int64_t) * (B1 - 1))) ||
         !cuda_ok(cudaMalloc(&p->d_in_len, sizeof(int64_t) * (B1 - 1))) ||
         !cuda_ok(cudaMalloc(&p->d_err, sizeof(int))) ||
@@ -1289,6 +1314,8 @@ hs_status hs_plan_create(hs_plan *out, const hs_desc *desc, int device)
         !cuda_ok(cudaMemcpy(p->d_in_len, p->len.data(), sizeof(int64_t) * (B1 - 1), cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemcpy(p->d_nf_main, p->nf_main.data(), sizeof(int64_t) * (B1 - 1), cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemcpy(p->d_tail_tile_start, p->tail_tile_start.data(), sizeof(int64_t) * B1,
+                            cudaMemcpyHostToDevice)) ||
+        !cuda_ok(cudaMemcpy(p->d_tail1_tile_start, p->tail1_tile_start.data(), sizeof(int64_t) * B1,
                             cudaMemcpyHostToDevice)) ||
         !cuda_ok(cudaMemset(p->d_err, 0, sizeof(int)))) {
         free_plan(p);

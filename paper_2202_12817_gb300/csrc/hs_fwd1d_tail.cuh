@@ -36,8 +36,11 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
     const int s = tile_spectrum(a.tail_tile_start, a.B, tile, a.tail_tiles_per_spec, a.inv_tail_tiles_per_spec);
     const int64_t t0 = __ldg(a.tail_tile_start + s), t1 = __ldg(a.tail_tile_start + s + 1);
     const int64_t fbase = __ldg(a.fund_off + s);
-    const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1
     const int64_t len = __ldg(a.in_len + s);
+    // this kernel's fundamentals end at n1 = floor((N - 1) / 2) + 1 (or N - 1); from n1 on both forms
+    // keep order 1 only, and k_fwd1d_tail1 runs them
+    const int64_t n_all = __ldg(a.fund_off + s + 1) - fbase, n1 = (len - 1) / 2 + 1;
+    const int64_t nf = n_all < n1 ? n_all : n1;
     const int64_t nbase = __ldg(a.nf_main + s) + (tile - t0) * (static_cast<int64_t>(blockDim.x) * CH) + threadIdx.x;
     const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
     const float *wv = a.w;
@@ -152,9 +155,99 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
     }
 }
 
-template <typename T>
-static const void *fwd1d_tail_kernel_for(int forms, int whitening)
+// ---------------------------------------------------------------------------------------
+// kernel: the one-order part of the truncated tail, max(n1, N_f) <= n < N - 1 with
+// n1 = floor((N - 1) / 2) + 1: there h n > N - 1 for h >= 2, so both forms keep order 1 only
+// (greedy: its mitigation comparison of x[n] and x[n + 1]).  The same steps as k_fwd1d_tail's
+// order 1, streamed: a CTA per kTail1Tile consecutive fundamentals of one spectrum, coalesced loads
+// and stores, one argmax update per form and CTA.
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
 {
+    constexpr int CH = kTail1Tile / kTailThreads;
+    __shared__ unsigned long long red[32];
+    constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
+    constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
+    const int H = a.H;
+    const int64_t tile = blockIdx.x;
+    const int s = tile_spectrum(a.tail1_tile_start, a.B, tile, a.tail1_tiles_per_spec, a.inv_tail1_tiles_per_spec);
+    const int64_t t0 = __ldg(a.tail1_tile_start + s);
+    const int64_t fbase = __ldg(a.fund_off + s);
+    const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1
+    const int64_t len = __ldg(a.in_len + s), nm = __ldg(a.nf_main + s), n1 = (len - 1) / 2 + 1;
+    const int64_t start = n1 > nm ? n1 : nm;
+    const int64_t nbase = start + (tile - t0) * kTail1Tile + threadIdx.x;
+    const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
+    const float *wv = a.w;
+    // order 1's normalisation, formed as the other kernels form it (1/sigma rounded, mu/sigma as mu * that)
+    const int64_t no = a.per_spectrum_norm ? static_cast<int64_t>(s) * H : 0;
+    float rs_s = 0.f, mr_s = 0.f, rs_g = 0.f, mr_g = 0.f;
+    if (kS) {
+        rs_s = __frcp_rn(__ldg(a.s.sigma + no));
+        mr_s = __fmul_rn(__ldg(a.s.mu + no), rs_s);
+    }
+    if (kG) {
+        rs_g = __frcp_rn(__ldg(a.g.sigma + no));
+        mr_g = __fmul_rn(__ldg(a.g.mu + no), rs_g);
+    }
+    float x0[CH], x1[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int64_t n = nbase + static_cast<int64_t>(c) * kTailThreads;
+        const uint32_t n32 = n < nf ? static_cast<uint32_t>(n) : 0u;
+        x0[c] = n < nf ? ld_x<T, WHITEN>(x, wv, n32) : 0.f;
+        x1[c] = (kG && a.mitigation && n < nf) ? ld_x<T, WHITEN>(x, wv, n32 + 1) : x0[c];
+    }
+    unsigned long long ks = 0ull, kg = 0ull;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int64_t n = nbase + static_cast<int64_t>(c) * kTailThreads;
+        if (n >= nf) continue;
+        const int64_t o = fbase + n;
+        if (kS) {
+            const float snr = fmaf(x0[c], rs_s, -mr_s);
+            a.s.snr[o] = snr;
+            a.s.best_h[o] = 1;
+            const unsigned long long k = argmax_key(snr, n);
+            ks = k > ks ? k : ks;
+        }
+        if (kG) {
+            const bool inc = x1[c] > x0[c];
+            const float snr = fmaf(inc ? x1[c] : x0[c], rs_g, -mr_g);
+            a.g.snr[o] = snr;
+            a.g.best_h[o] = 1;
+            if (a.g.path) store_path(a.g.path, a.path_bytes, o, inc ? 1u : 0u);
+            const unsigned long long k = argmax_key(snr, n);
+            kg = k > kg ? k : kg;
+        }
+    }
+    if (kS && a.s.argmax) block_argmax(ks, a.s.argmax + s, red);
+    if (kG && a.g.argmax) {
+        if (kS && a.s.argmax) __syncthreads();
+        block_argmax(kg, a.g.argmax + s, red);
+    }
+}
+
+template <typename T>
+static const void *fwd1d_tail_kernel_for(int forms, int whitening, int one_order)
+{
+    if (one_order) {
+        if (whitening) {
+            switch (forms) {
+            case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 1, true>);
+            case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 2, true>);
+            case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 3, true>);
+            }
+        } else {
+            switch (forms) {
+            case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 1, false>);
+            case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 2, false>);
+            case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 3, false>);
+            }
+        }
+        return nullptr;
+    }
     if (whitening) {
         switch (forms) {
         case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, true>);

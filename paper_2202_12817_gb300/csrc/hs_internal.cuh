@@ -38,16 +38,22 @@ struct Fwd1DArgs {
     const int64_t *in_off;         // [B+1] element offset of each spectrum
     const int64_t *fund_off;       // [B+1] output offset of each spectrum (prefix of its fundamentals)
     const int64_t *nf_main;        // [B] fundamentals with all H orders, N_f = floor((N-1)/H)
-    const int64_t *tail_tile_start;// [B+1] prefix of truncated-tail tiles (HS_FLAG_TRUNCATE_TAIL)
+    const int64_t *tail_tile_start;// [B+1] prefix of truncated-tail tiles (HS_FLAG_TRUNCATE_TAIL): the
+                                   // fundamentals N_f <= n < min(N - 1, n1), n1 = floor((N - 1) / 2) + 1
     int64_t tail_tiles;            // total truncated-tail tiles (0 without the flag)
+    const int64_t *tail1_tile_start;// [B+1] prefix of one-order tail tiles: max(n1, N_f) <= n < N - 1,
+                                   // where both forms keep order 1 only
+    int64_t tail1_tiles;           // total one-order tail tiles
     const int64_t *tile_start;     // [B+1] prefix of tiles per spectrum
     const int64_t *in_len;         // [B] N_s (for checked mode)
     int32_t B;
     uint32_t tiles_per_spec;       // > 0: every spectrum has this many main-pass tiles (one length for
                                    // all, fewer than 2^22 tiles in all)
     uint32_t tail_tiles_per_spec;  // > 0: likewise for the truncated-tail tiles
-    float inv_tiles_per_spec;      // fl(1 / tiles_per_spec), fl(1 / tail_tiles_per_spec)
+    uint32_t tail1_tiles_per_spec; // > 0: likewise for the one-order tail tiles
+    float inv_tiles_per_spec;      // fl(1 / tiles_per_spec), fl(1 / tail_tiles_per_spec), ...
     float inv_tail_tiles_per_spec;
+    float inv_tail1_tiles_per_spec;
     int32_t H;
     int32_t mitigation;
     int32_t per_spectrum_norm;
@@ -145,12 +151,14 @@ const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel(int dtype);
 const void *wait_selftest_kernel();
 const void *fwd1d_opt_kernel(int dtype, int whitening, int H, int tail);
-// 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 per CTA
-const void *fwd1d_tail_kernel_f32(int forms, int whitening);
-const void *fwd1d_tail_kernel_f16(int forms, int whitening);
-const void *fwd1d_tail_kernel_bf16(int forms, int whitening);
+// 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 threads per CTA;
+// one_order selects the kernel of the fundamentals whose forms keep order 1 only (n >= n1)
+const void *fwd1d_tail_kernel_f32(int forms, int whitening, int one_order);
+const void *fwd1d_tail_kernel_f16(int forms, int whitening, int one_order);
+const void *fwd1d_tail_kernel_bf16(int forms, int whitening, int one_order);
 constexpr int kTailThreads = 256;
 constexpr int kTailTile = 1024;     // truncated-tail fundamentals per tile (kTailThreads x 4 per thread)
+constexpr int kTail1Tile = 2048;    // one-order tail fundamentals per tile (kTailThreads x 8 per thread)
 const void *bwd1d_kernel(int form, int dtype, int whitening);
 const void *bwd_dw_reduce_kernel();
 const void *bwd_mark_kernel(int form);
