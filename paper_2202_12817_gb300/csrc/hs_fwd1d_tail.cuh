@@ -1,6 +1,8 @@
 // Truncated tail of the 1D forward (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1.
 #pragma once
 
+#include <type_traits>
+
 #include "hs_fwd1d.cuh"
 
 namespace hs {
@@ -159,13 +161,33 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
 // kernel: the one-order part of the truncated tail, max(n1, N_f) <= n < N - 1 with
 // n1 = floor((N - 1) / 2) + 1: there h n > N - 1 for h >= 2, so both forms keep order 1 only
 // (greedy: its mitigation comparison of x[n] and x[n + 1]).  The same steps as k_fwd1d_tail's
-// order 1, streamed: a CTA per kTail1Tile consecutive fundamentals of one spectrum, coalesced loads
-// and stores, one argmax update per form and CTA.
+// order 1, streamed: a CTA per kTail1Tile consecutive fundamentals of one spectrum in rounds of
+// kTailThreads x kTail1Chains, each round's loads issued before the previous round's stores, so
+// one DRAM latency per round overlaps the other's work; coalesced loads and stores, one argmax
+// update per form and CTA.
 // ---------------------------------------------------------------------------------------
+constexpr int kTail1Chains = 4;     // one-order fundamentals per thread and round
+constexpr int kTail1Rounds = kTail1Tile / (kTailThreads * kTail1Chains);
+static_assert(kTail1Rounds * kTailThreads * kTail1Chains == kTail1Tile, "one-order tile and rounds disagree");
+
+// One round's loads: x[n] and, for the greedy mitigation, x[n + 1] of the thread's fundamentals.
+template <typename T, bool WHITEN, bool MIT>
+__device__ __forceinline__ void tail1_load(const T *x, const float *wv, uint32_t nb, uint32_t nf, float (&x0)[kTail1Chains],
+                                           float (&x1)[kTail1Chains])
+{
+#pragma unroll
+    for (int c = 0; c < kTail1Chains; ++c) {
+        const uint32_t n = nb + c * kTailThreads;
+        const uint32_t nl = n < nf ? n : 0u;
+        x0[c] = n < nf ? ld_x<T, WHITEN>(x, wv, nl) : 0.f;
+        x1[c] = MIT && n < nf ? ld_x<T, WHITEN>(x, wv, nl + 1) : x0[c];
+    }
+}
+
 template <typename T, int FORMS, bool WHITEN>
 __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
 {
-    constexpr int CH = kTail1Tile / kTailThreads;
+    constexpr int CH = kTail1Chains;
     __shared__ unsigned long long red[32];
     constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
     constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
@@ -174,10 +196,11 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
     const int s = tile_spectrum(a.tail1_tile_start, a.B, tile, a.tail1_tiles_per_spec, a.inv_tail1_tiles_per_spec);
     const int64_t t0 = __ldg(a.tail1_tile_start + s);
     const int64_t fbase = __ldg(a.fund_off + s);
-    const int64_t nf = __ldg(a.fund_off + s + 1) - fbase;   // N - 1
-    const int64_t len = __ldg(a.in_len + s), nm = __ldg(a.nf_main + s), n1 = (len - 1) / 2 + 1;
-    const int64_t start = n1 > nm ? n1 : nm;
-    const int64_t nbase = start + (tile - t0) * kTail1Tile + threadIdx.x;
+    const int64_t len = __ldg(a.in_len + s);
+    // N < 2^31, so every bin index of the spectrum fits in 32 bits
+    const uint32_t nf = static_cast<uint32_t>(len - 1);   // N - 1
+    const uint32_t n1 = static_cast<uint32_t>((len - 1) / 2 + 1), nm = static_cast<uint32_t>(__ldg(a.nf_main + s));
+    const uint32_t nbase = (n1 > nm ? n1 : nm) + static_cast<uint32_t>(tile - t0) * kTail1Tile + threadIdx.x;
     const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
     const float *wv = a.w;
     // order 1's normalisation, formed as the other kernels form it (1/sigma rounded, mu/sigma as mu * that)
@@ -191,37 +214,62 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
         rs_g = __frcp_rn(__ldg(a.g.sigma + no));
         mr_g = __fmul_rn(__ldg(a.g.mu + no), rs_g);
     }
-    float x0[CH], x1[CH];
+    float *snr_s = kS ? a.s.snr + fbase : nullptr;
+    float *snr_g = kG ? a.g.snr + fbase : nullptr;
+    uint8_t *bh_s = kS ? a.s.best_h + fbase : nullptr;
+    uint8_t *bh_g = kG ? a.g.best_h + fbase : nullptr;
+    const int pb = kG && a.g.path ? a.path_bytes : 0;
+    unsigned char *pth = pb ? static_cast<unsigned char *>(a.g.path) + fbase * pb : nullptr;
+    // per-thread argmax as (ordered SNR bits, bin): a thread's bins ascend, so a strictly larger
+    // value replaces and equal values keep the lower bin, as the 64-bit key order does
+    uint32_t os = 0u, og = 0u, bs = 0xffffffffu, bg = 0xffffffffu;
+    const auto body = [&](uint32_t nb, const float (&x0)[CH], const float (&x1)[CH]) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-        const int64_t n = nbase + static_cast<int64_t>(c) * kTailThreads;
-        const uint32_t n32 = n < nf ? static_cast<uint32_t>(n) : 0u;
-        x0[c] = n < nf ? ld_x<T, WHITEN>(x, wv, n32) : 0.f;
-        x1[c] = (kG && a.mitigation && n < nf) ? ld_x<T, WHITEN>(x, wv, n32 + 1) : x0[c];
-    }
-    unsigned long long ks = 0ull, kg = 0ull;
+        for (int c = 0; c < CH; ++c) {
+            const uint32_t n = nb + c * kTailThreads;
+            if (n >= nf) continue;
+            const float v0 = x0[c], v1 = x1[c];
+            if (kS) {
+                const float snr = fmaf(v0, rs_s, -mr_s);
+                snr_s[n] = snr;
+                bh_s[n] = 1;
+                const uint32_t o = ordered_bits(snr);
+                if (bs == 0xffffffffu || o > os) { os = o; bs = n; }
+            }
+            if (kG) {
+                const bool inc = v1 > v0;
+                const float snr = fmaf(inc ? v1 : v0, rs_g, -mr_g);
+                snr_g[n] = snr;
+                bh_g[n] = 1;
+                if (pb == 4) reinterpret_cast<uint32_t *>(pth)[n] = inc ? 1u : 0u;
+                else if (pb == 2) reinterpret_cast<uint16_t *>(pth)[n] = inc ? 1u : 0u;
+                else if (pb == 1) pth[n] = inc ? 1u : 0u;
+                const uint32_t o = ordered_bits(snr);
+                if (bg == 0xffffffffu || o > og) { og = o; bg = n; }
+            }
+        }
+    };
+    // rounds alternate between two register sets: round r + 1's loads go out before round r's stores
+    const auto rounds = [&](auto mit) {
+        constexpr bool M = decltype(mit)::value;
+        constexpr uint32_t R = kTailThreads * CH;
+        float xa0[CH], xa1[CH], xb0[CH], xb1[CH];
+        tail1_load<T, WHITEN, M>(x, wv, nbase, nf, xa0, xa1);
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-        const int64_t n = nbase + static_cast<int64_t>(c) * kTailThreads;
-        if (n >= nf) continue;
-        const int64_t o = fbase + n;
-        if (kS) {
-            const float snr = fmaf(x0[c], rs_s, -mr_s);
-            a.s.snr[o] = snr;
-            a.s.best_h[o] = 1;
-            const unsigned long long k = argmax_key(snr, n);
-            ks = k > ks ? k : ks;
+        for (int r = 0; r < kTail1Rounds; r += 2) {
+            const uint32_t nb = nbase + r * R;
+            if (r + 1 < kTail1Rounds) tail1_load<T, WHITEN, M>(x, wv, nb + R, nf, xb0, xb1);
+            body(nb, xa0, xa1);
+            if (r + 1 < kTail1Rounds) {
+                if (r + 2 < kTail1Rounds) tail1_load<T, WHITEN, M>(x, wv, nb + 2 * R, nf, xa0, xa1);
+                body(nb + R, xb0, xb1);
+            }
         }
-        if (kG) {
-            const bool inc = x1[c] > x0[c];
-            const float snr = fmaf(inc ? x1[c] : x0[c], rs_g, -mr_g);
-            a.g.snr[o] = snr;
-            a.g.best_h[o] = 1;
-            if (a.g.path) store_path(a.g.path, a.path_bytes, o, inc ? 1u : 0u);
-            const unsigned long long k = argmax_key(snr, n);
-            kg = k > kg ? k : kg;
-        }
-    }
+    };
+    if (kG && a.mitigation) rounds(std::true_type{});
+    else rounds(std::false_type{});
+    const unsigned long long ks = bs == 0xffffffffu ? 0ull : (static_cast<unsigned long long>(os) << 32) | (0xffffffffu - bs);
+    const unsigned long long kg = bg == 0xffffffffu ? 0ull : (static_cast<unsigned long long>(og) << 32) | (0xffffffffu - bg);
     if (kS && a.s.argmax) block_argmax(ks, a.s.argmax + s, red);
     if (kG && a.g.argmax) {
         if (kS && a.s.argmax) __syncthreads();

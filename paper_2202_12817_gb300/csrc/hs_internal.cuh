@@ -158,7 +158,7 @@ const void *fwd1d_tail_kernel_f16(int forms, int whitening, int one_order);
 const void *fwd1d_tail_kernel_bf16(int forms, int whitening, int one_order);
 constexpr int kTailThreads = 256;
 constexpr int kTailTile = 1024;     // truncated-tail fundamentals per tile (kTailThreads x 4 per thread)
-constexpr int kTail1Tile = 2048;    // one-order tail fundamentals per tile (kTailThreads x 8 per thread)
+constexpr int kTail1Tile = 8192;    // one-order tail fundamentals per tile (eight rounds of kTailThreads x 4)
 const void *bwd1d_kernel(int form, int dtype, int whitening);
 const void *bwd_dw_reduce_kernel();
 const void *bwd_mark_kernel(int form);
