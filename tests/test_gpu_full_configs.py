@@ -182,3 +182,52 @@ def test_training_step_256x2p20_full_size(hs, oracle_lib):
         checked += 1
     assert checked >= 64 and flipped <= checked // 4, (checked, flipped)
     plan.close()
+
+
+@pytest.mark.parametrize("every_bin", [False, True], ids=["full_harmonic", "every_bin"])
+def test_table2_batch_1024x131072_full_size(hs, oracle_lib, every_bin):
+    """The paper's throughput configuration (Table 2): 1024 FP32 spectra of 131072 bins, H = 32,
+    greedy, built as the benchmark builds it (Exp(1) noise and one pulsar per spectrum), autotuned,
+    over the fundamentals with all H orders or with the truncated tail (every bin but the last a
+    fundamental: the generic tail kernel up to n1 = floor((N - 1) / 2) + 1, the one-order kernel
+    above, 8 one-order tiles per spectrum found by division).  A seeded sample of 24 spectra plus
+    the first and the last is compared with the oracle element by element, paths and argmax
+    included."""
+    B, N, H = 1024, 1 << 17, 32
+    lengths = np.full(B, N, np.int64)
+    offsets = synth.pack_offsets(lengths, 32)
+    x = torch.zeros(int(offsets[-1]), dtype=torch.float32, device=DEV)
+    for i in range(B):
+        view = x[int(offsets[i]):int(offsets[i]) + N]
+        synth.device_noise(N, synth.SEED_BASE + 6 + 13 * i, DEV, out=view)
+        synth.device_inject(view, [synth.random_pulsars(1, N, synth.SEED_BASE + 6000 + i)[0]])
+    flags = hs.FLAG_AUTOTUNE | (hs.FLAG_TRUNCATE_TAIL if every_bin else 0)
+    plan = hs.Plan(H, hs.GREEDY, lengths=lengths, offsets=offsets[:-1], flags=flags, device=0)
+    mu, sg = hs.norm_exponential(hs.GREEDY, 1, H)
+    io = plan.alloc_form(torch.from_numpy(mu).to(DEV), torch.from_numpy(sg).to(DEV), path=True, argmax=True)
+    ws = None if not plan.workspace_bytes else plan.workspace(DEV)
+    hs.run(plan, x, None, None, io, ws, torch.cuda.current_stream(DEV))
+    torch.cuda.synchronize()
+    hs.check_device_error(plan)
+    fo = plan.fund_offsets
+    assert int(fo[1] - fo[0]) == (N - 1 if every_bin else (N - 1) // H)
+    pick = sorted(set(np.random.default_rng(2024).choice(np.arange(1, B - 1), 24, replace=False).tolist()) | {0, B - 1})
+    key = io.argmax.cpu().numpy()
+    near = compared = 0
+    for i in pick:
+        xs = x[int(offsets[i]):int(offsets[i]) + N].cpu().numpy()
+        r_snr, r_bh, r_path, r_all = oracle_lib.greedy_1d(xs, H, mu, sg, want_all=True)
+        if every_bin:
+            ts, tb, tp, ta = oracle_lib.tail_1d(2, xs, H, mu, sg, want_all=True)
+            ta = np.where(np.isnan(ta), -np.inf, ta)   # orders that do not fit can never be the best
+            r_snr, r_bh = np.concatenate([r_snr, ts]), np.concatenate([r_bh, tb])
+            r_path, r_all = np.concatenate([r_path, tp]), np.concatenate([r_all, ta])
+        a, e = int(fo[i]), int(fo[i + 1])
+        assert e - a == r_snr.shape[0]
+        g_snr, g_bh = io.snr[a:e].cpu().numpy(), io.best_h[a:e].cpu().numpy()
+        near += compare_form(g_snr, g_bh, r_snr, r_bh, r_all, mu, sg, path_view(io.path[a:e], H), r_path,
+                             what=f"spectrum {i}")
+        compare_argmax(key[i], r_snr, g_snr, mu, sg, r_bh, hs.decode_argmax, what=f"argmax {i}")
+        compared += e - a
+    assert near <= 1e-4 * compared, (near, compared)
+    plan.close()

@@ -31,10 +31,11 @@ def oracle_full(o, form, x, H, mu, sg, mitigation, w):
             None if p is None else np.concatenate([p, tp]), np.concatenate([a, ta]))
 
 
-def tail_case(hs, o, spectra, H, forms, mitigation=True, dtype=0, w=None, tuning=None):
+def tail_case(hs, o, spectra, H, forms, mitigation=True, dtype=0, w=None, tuning=None, per_spec_norm=False):
     lengths = [len(s) for s in spectra]
     flags = hs.FLAG_TRUNCATE_TAIL | (0 if mitigation else hs.FLAG_NO_MITIGATION)
     flags |= hs.FLAG_WHITENING if w is not None else 0
+    flags |= hs.FLAG_PER_SPECTRUM_NORM if per_spec_norm else 0
     plan = hs.Plan(H, forms, lengths=lengths, dtype=dtype, flags=flags)
     if tuning is not None:
         plan.tuning = tuning
@@ -53,6 +54,10 @@ def tail_case(hs, o, spectra, H, forms, mitigation=True, dtype=0, w=None, tuning
                 sg = np.sqrt(np.linspace(1.3, 1.3 * H, H)).astype(np.float32)
             else:
                 mu, sg = hs.norm_exponential(f, 1, H, mitigation)
+            if per_spec_norm:   # one row per spectrum, scaled per spectrum
+                g = np.random.default_rng(77 + f)
+                mu = (mu[None, :] * g.uniform(0.8, 1.2, (len(spectra), 1))).astype(np.float32)
+                sg = (sg[None, :] * g.uniform(0.8, 1.2, (len(spectra), 1))).astype(np.float32)
             norms[f] = (mu, sg)
     dn = {f: (torch.from_numpy(m).to(DEV), torch.from_numpy(s).to(DEV)) for f, (m, s) in norms.items()}
     wd = None if w is None else torch.from_numpy(w).to(DEV)
@@ -63,6 +68,8 @@ def tail_case(hs, o, spectra, H, forms, mitigation=True, dtype=0, w=None, tuning
         a, b = int(plan.fund_offsets[s]), int(plan.fund_offsets[s + 1])
         for f in norms:
             mu, sg = norms[f]
+            if per_spec_norm:
+                mu, sg = mu[s], sg[s]
             r_snr, r_bh, r_path, r_all = oracle_full(o, f, x, H, mu, sg, mitigation, w)
             io = out[f]
             g_path = path_view(io.path, H)[a:b] if f == 2 else None
@@ -90,6 +97,14 @@ def test_tail_batch_dtypes_and_shapes(hs, oracle_lib, dtype):
         plan, _, _ = tail_case(hs, oracle_lib, xs, 32, hs.SIMPLE | hs.GREEDY, dtype=dtype, tuning=t)
         plan.close()
     plan, _, _ = tail_case(hs, oracle_lib, xs, 8, hs.GREEDY, dtype=dtype)
+    plan.close()
+
+
+def test_tail_per_spectrum_norm(hs, oracle_lib):
+    """Per-spectrum normalisation rows reach both tail kernels (the generic one and the one-order
+    one), several one-order tiles per spectrum, uneven lengths."""
+    xs = [synth.spectrum(n, 500 + n % 17, [synth.Pulsar(41.3, 0.06)]) for n in (5000, 40000, 20011, 9000)]
+    plan, _, _ = tail_case(hs, oracle_lib, xs, 16, hs.SIMPLE | hs.GREEDY, per_spec_norm=True)
     plan.close()
 
 
