@@ -512,12 +512,12 @@ FormArgs to_form_args(const hs_form_io *io)
     return f;
 }
 
-const void *fwd1d_tail_kernel(int dtype, int forms, int whitening, int one_order)
+const void *fwd1d_tail_kernel(int dtype, int forms, int whitening)
 {
     switch (dtype) {
-    case HS_F32: return fwd1d_tail_kernel_f32(forms, whitening, one_order);
-    case HS_F16: return fwd1d_tail_kernel_f16(forms, whitening, one_order);
-    case HS_BF16: return fwd1d_tail_kernel_bf16(forms, whitening, one_order);
+    case HS_F32: return fwd1d_tail_kernel_f32(forms, whitening);
+    case HS_F16: return fwd1d_tail_kernel_f16(forms, whitening);
+    case HS_BF16: return fwd1d_tail_kernel_bf16(forms, whitening);
     }
     return nullptr;
 }
@@ -546,29 +546,23 @@ hs_status launch_fwd(const void *fn, dim3 grid, dim3 block, void **args, size_t 
     return HS_OK;
 }
 
-// The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel --
-// those below n1 = floor((N - 1) / 2) + 1 first, then the one-order rest.
+// The truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, after the main kernel,
+// in one launch: the generic tiles (below n1 = floor((N - 1) / 2) + 1) and the one-order tiles.
 hs_status launch_tail(const hs_plan p, const Fwd1DArgs &main_args, cudaStream_t st, bool prewhitened = false)
 {
     if (!(p->d.flags & HS_FLAG_TRUNCATE_TAIL)) return HS_OK;
-    if (main_args.tail_tiles > 0x7fffffff || main_args.tail1_tiles > 0x7fffffff) return HS_ERR_UNSUPPORTED;
+    const int64_t ctas = main_args.tail_tiles + main_args.tail1_tiles;
+    if (ctas <= 0) return HS_OK;
+    if (ctas > 0x7fffffff) return HS_ERR_UNSUPPORTED;
     // on the pre-whitened copy the tail reads plain FP32
-    const int dt = prewhitened ? HS_F32 : p->d.dtype;
-    const int wh = (!prewhitened && (p->d.flags & HS_FLAG_WHITENING)) ? 1 : 0;
+    const void *fn = prewhitened ? fwd1d_tail_kernel(HS_F32, p->d.forms & 3, 0)
+                                 : fwd1d_tail_kernel(p->d.dtype, p->d.forms & 3, (p->d.flags & HS_FLAG_WHITENING) ? 1 : 0);
+    if (!fn) return HS_ERR_UNSUPPORTED;
     Fwd1DArgs a = main_args;
     a.tile_counter = nullptr;
     a.pf_chunk = 0;
     void *args[] = {&a};
-    if (a.tail_tiles > 0) {
-        const void *fn = fwd1d_tail_kernel(dt, p->d.forms & 3, wh, 0);
-        if (!fn) return HS_ERR_UNSUPPORTED;
-        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail_tiles)), dim3(kTailThreads), args, 0, st));
-    }
-    if (a.tail1_tiles > 0) {
-        const void *fn = fwd1d_tail_kernel(dt, p->d.forms & 3, wh, 1);
-        if (!fn) return HS_ERR_UNSUPPORTED;
-        HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(a.tail1_tiles)), dim3(kTailThreads), args, 0, st));
-    }
+    HS_CUDA(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(ctas)), dim3(kTailThreads), args, 0, st));
     return HS_OK;
 }
 

@@ -9,8 +9,8 @@ const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel)
 {
     return fwd1d_kernel_for<__nv_bfloat16>(forms, whitening, kernel);
 }
-const void *fwd1d_tail_kernel_bf16(int forms, int whitening, int one_order)
+const void *fwd1d_tail_kernel_bf16(int forms, int whitening)
 {
-    return fwd1d_tail_kernel_for<__nv_bfloat16>(forms, whitening, one_order);
+    return fwd1d_tail_kernel_for<__nv_bfloat16>(forms, whitening);
 }
 }  // namespace hs

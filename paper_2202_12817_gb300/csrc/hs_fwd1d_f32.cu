@@ -9,8 +9,8 @@ const void *fwd1d_kernel_f32(int forms, int whitening, int kernel)
 {
     return fwd1d_kernel_for<float>(forms, whitening, kernel);
 }
-const void *fwd1d_tail_kernel_f32(int forms, int whitening, int one_order)
+const void *fwd1d_tail_kernel_f32(int forms, int whitening)
 {
-    return fwd1d_tail_kernel_for<float>(forms, whitening, one_order);
+    return fwd1d_tail_kernel_for<float>(forms, whitening);
 }
 }  // namespace hs

@@ -12,35 +12,33 @@ constexpr int kTailAhead = 8;       // the tail prefetches the spectrum this man
 static_assert(kTailTile == kTailThreads * kTailChains, "host tail tiling and kernel chains disagree");
 
 // ---------------------------------------------------------------------------------------
-// kernel: the truncated tail (HS_FLAG_TRUNCATE_TAIL), fundamentals N_f <= n < N - 1 whose
-// higher orders would read past the end of the spectrum.  Each form keeps the orders whose
-// every possible read fits: simple h n <= N - 1, greedy h n + h <= N - 1 (drift at most h - 1
-// after order h - 1, plus the compared neighbour).  Both forms in one thread; a CTA per
-// kTailThreads x kTailChains consecutive tail fundamentals of one spectrum.
+// The truncated tail (HS_FLAG_TRUNCATE_TAIL), fundamentals N_f <= n < N - 1 whose higher
+// orders would read past the end of the spectrum.  Each form keeps the orders whose every
+// possible read fits: simple h n <= N - 1, greedy h n + h <= N - 1 (drift at most h - 1 after
+// order h - 1, plus the compared neighbour).  Two kinds of tile, run by one kernel
+// (k_fwd1d_tail): below n1 = floor((N - 1) / 2) + 1 the orders that fit vary (tail_orders);
+// from n1 on both forms keep order 1 only (tail_one_order).
 // ---------------------------------------------------------------------------------------
+
+// Generic tile `tile` (of the tail_tile_start numbering) of spectrum s: kTailThreads x
+// kTailChains consecutive fundamentals N_f <= n < n1, both forms in one thread.  Most of them
+// have a few orders only, so a thread's time is a short chain of dependent loads: each thread
+// runs kTailChains fundamentals (n, n + T, ...) interleaved order by order to keep that many
+// chains in flight.  The tiles of spectrum s bring spectrum s - kTailAhead into L2, one share
+// each.
 template <typename T, int FORMS, bool WHITEN>
-__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
+__device__ __forceinline__ void tail_orders(const Fwd1DArgs &a, const int s, const int64_t tile, NormSmem &nm,
+                                            unsigned long long *red)
 {
-    // Truncated tail: fundamentals N_f <= n < N - 1, each form with the orders whose reads stay
-    // below N (simple h n <= N - 1, greedy h n + h <= N - 1).  Most of these fundamentals have a
-    // few orders only, so a thread's time is a short chain of dependent loads: each thread runs
-    // kTailChains fundamentals (n, n + T, ...) interleaved order by order to keep that many
-    // chains in flight.  Tiles run in decreasing spectrum order -- the main pass that precedes
-    // this kernel leaves the last spectra in L2 -- and the tiles of spectrum s bring spectrum
-    // s - kTailAhead into L2, one share each.
     constexpr int CH = kTailChains;
-    __shared__ NormSmem nm;
-    __shared__ unsigned long long red[32];
     constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
     constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
     const int H = a.H;
-    const int64_t tile = a.tail_tiles - 1 - static_cast<int64_t>(blockIdx.x);
-    const int s = tile_spectrum(a.tail_tile_start, a.B, tile, a.tail_tiles_per_spec, a.inv_tail_tiles_per_spec);
     const int64_t t0 = __ldg(a.tail_tile_start + s), t1 = __ldg(a.tail_tile_start + s + 1);
     const int64_t fbase = __ldg(a.fund_off + s);
     const int64_t len = __ldg(a.in_len + s);
-    // this kernel's fundamentals end at n1 = floor((N - 1) / 2) + 1 (or N - 1); from n1 on both forms
-    // keep order 1 only, and k_fwd1d_tail1 runs them
+    // these fundamentals end at n1 = floor((N - 1) / 2) + 1 (or N - 1); from n1 on both forms keep
+    // order 1 only (tail_one_order)
     const int64_t n_all = __ldg(a.fund_off + s + 1) - fbase, n1 = (len - 1) / 2 + 1;
     const int64_t nf = n_all < n1 ? n_all : n1;
     const int64_t nbase = __ldg(a.nf_main + s) + (tile - t0) * (static_cast<int64_t>(blockDim.x) * CH) + threadIdx.x;
@@ -157,15 +155,12 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// kernel: the one-order part of the truncated tail, max(n1, N_f) <= n < N - 1 with
-// n1 = floor((N - 1) / 2) + 1: there h n > N - 1 for h >= 2, so both forms keep order 1 only
-// (greedy: its mitigation comparison of x[n] and x[n + 1]).  The same steps as k_fwd1d_tail's
-// order 1, streamed: a CTA per kTail1Tile consecutive fundamentals of one spectrum in rounds of
-// kTailThreads x kTail1Chains, each round's loads issued before the previous round's stores, so
-// one DRAM latency per round overlaps the other's work; coalesced loads and stores, one argmax
-// update per form and CTA.
-// ---------------------------------------------------------------------------------------
+// One-order tiles: max(n1, N_f) <= n < N - 1 with n1 = floor((N - 1) / 2) + 1, where h n > N - 1
+// for h >= 2, so both forms keep order 1 only (greedy: its mitigation comparison of x[n] and
+// x[n + 1]).  The same steps as tail_orders' order 1, streamed: kTail1Tile consecutive
+// fundamentals of one spectrum in rounds of kTailThreads x kTail1Chains, each round's loads
+// issued before the previous round's stores, so one DRAM latency per round overlaps the other's
+// work; coalesced loads and stores, one argmax update per form and CTA.
 constexpr int kTail1Chains = 4;     // one-order fundamentals per thread and round
 constexpr int kTail1Rounds = kTail1Tile / (kTailThreads * kTail1Chains);
 static_assert(kTail1Rounds * kTailThreads * kTail1Chains == kTail1Tile, "one-order tile and rounds disagree");
@@ -184,16 +179,15 @@ __device__ __forceinline__ void tail1_load(const T *x, const float *wv, uint32_t
     }
 }
 
+// One-order tile `tile` (of the tail1_tile_start numbering) of spectrum s.
 template <typename T, int FORMS, bool WHITEN>
-__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
+__device__ __forceinline__ void tail_one_order(const Fwd1DArgs &a, const int s, const int64_t tile,
+                                               unsigned long long *red)
 {
     constexpr int CH = kTail1Chains;
-    __shared__ unsigned long long red[32];
     constexpr bool kS = (FORMS & HS_FORM_SIMPLE) != 0;
     constexpr bool kG = (FORMS & HS_FORM_GREEDY) != 0;
     const int H = a.H;
-    const int64_t tile = blockIdx.x;
-    const int s = tile_spectrum(a.tail1_tile_start, a.B, tile, a.tail1_tiles_per_spec, a.inv_tail1_tiles_per_spec);
     const int64_t t0 = __ldg(a.tail1_tile_start + s);
     const int64_t fbase = __ldg(a.fund_off + s);
     const int64_t len = __ldg(a.in_len + s);
@@ -277,25 +271,49 @@ __global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail1(const Fwd1DArgs a)
     }
 }
 
-template <typename T>
-static const void *fwd1d_tail_kernel_for(int forms, int whitening, int one_order)
+// ---------------------------------------------------------------------------------------
+// kernel: the whole truncated tail in one launch.  Spectrum s owns T_s = G_s + O_s consecutive
+// CTAs of the launch, its G_s generic tiles followed by its O_s one-order tiles; the CTAs run
+// from the last spectrum down (the main pass that precedes this kernel leaves the last spectra
+// in L2), and within a spectrum the one-order tiles, which stream, start with the generic ones,
+// whose chains of gathers are latency-bound, and read the same lines of the spectrum.
+// ---------------------------------------------------------------------------------------
+template <typename T, int FORMS, bool WHITEN>
+__global__ void __launch_bounds__(kTailThreads) k_fwd1d_tail(const Fwd1DArgs a)
 {
-    if (one_order) {
-        if (whitening) {
-            switch (forms) {
-            case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 1, true>);
-            case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 2, true>);
-            case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 3, true>);
-            }
+    __shared__ NormSmem nm;
+    __shared__ unsigned long long red[32];
+    const int64_t q = a.tail_tiles + a.tail1_tiles - 1 - static_cast<int64_t>(blockIdx.x);
+    // the spectrum whose CTAs hold q: by a division when every spectrum has the same tile counts,
+    // else a binary search over the summed prefixes
+    const unsigned per = a.tail_tiles_per_spec + a.tail1_tiles_per_spec;
+    int s = 0;
+    int64_t c0 = 0;
+    if (a.B > 1) {
+        if (per > 0) {
+            const unsigned u = static_cast<unsigned>(q) / per;
+            s = u < static_cast<unsigned>(a.B) ? static_cast<int>(u) : a.B - 1;
+            c0 = static_cast<int64_t>(s) * per;
         } else {
-            switch (forms) {
-            case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 1, false>);
-            case 2: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 2, false>);
-            case 3: return reinterpret_cast<const void *>(&k_fwd1d_tail1<T, 3, false>);
+            int lo = 0, hi = a.B - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(a.tail_tile_start + mid) + __ldg(a.tail1_tile_start + mid) <= q) lo = mid;
+                else hi = mid - 1;
             }
+            s = lo;
+            c0 = __ldg(a.tail_tile_start + s) + __ldg(a.tail1_tile_start + s);
         }
-        return nullptr;
     }
+    const int64_t g0 = __ldg(a.tail_tile_start + s), gn = __ldg(a.tail_tile_start + s + 1) - g0;
+    const int64_t j = q - c0;
+    if (j < gn) tail_orders<T, FORMS, WHITEN>(a, s, g0 + j, nm, red);
+    else tail_one_order<T, FORMS, WHITEN>(a, s, __ldg(a.tail1_tile_start + s) + (j - gn), red);
+}
+
+template <typename T>
+static const void *fwd1d_tail_kernel_for(int forms, int whitening)
+{
     if (whitening) {
         switch (forms) {
         case 1: return reinterpret_cast<const void *>(&k_fwd1d_tail<T, 1, true>);

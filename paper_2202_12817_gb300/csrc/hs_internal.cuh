@@ -151,11 +151,11 @@ const void *fwd1d_kernel_bf16(int forms, int whitening, int kernel);
 const void *fwd2d_kernel(int dtype);
 const void *wait_selftest_kernel();
 const void *fwd1d_opt_kernel(int dtype, int whitening, int H, int tail);
-// 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 threads per CTA;
-// one_order selects the kernel of the fundamentals whose forms keep order 1 only (n >= n1)
-const void *fwd1d_tail_kernel_f32(int forms, int whitening, int one_order);
-const void *fwd1d_tail_kernel_f16(int forms, int whitening, int one_order);
-const void *fwd1d_tail_kernel_bf16(int forms, int whitening, int one_order);
+// 1D truncated tail (HS_FLAG_TRUNCATE_TAIL): fundamentals N_f <= n < N - 1, 256 threads per CTA,
+// one CTA per generic tile and per one-order tile
+const void *fwd1d_tail_kernel_f32(int forms, int whitening);
+const void *fwd1d_tail_kernel_f16(int forms, int whitening);
+const void *fwd1d_tail_kernel_bf16(int forms, int whitening);
 constexpr int kTailThreads = 256;
 constexpr int kTailTile = 1024;     // truncated-tail fundamentals per tile (kTailThreads x 4 per thread)
 constexpr int kTail1Tile = 8192;    // one-order tail fundamentals per tile (eight rounds of kTailThreads x 4)

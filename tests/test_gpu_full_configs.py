@@ -189,8 +189,8 @@ def test_table2_batch_1024x131072_full_size(hs, oracle_lib, every_bin):
     """The paper's throughput configuration (Table 2): 1024 FP32 spectra of 131072 bins, H = 32,
     greedy, built as the benchmark builds it (Exp(1) noise and one pulsar per spectrum), autotuned,
     over the fundamentals with all H orders or with the truncated tail (every bin but the last a
-    fundamental: the generic tail kernel up to n1 = floor((N - 1) / 2) + 1, the one-order kernel
-    above, 8 one-order tiles per spectrum found by division).  A seeded sample of 24 spectra plus
+    fundamental: generic tail tiles up to n1 = floor((N - 1) / 2) + 1 and 8 one-order tiles above
+    it per spectrum, in one launch whose CTAs find their spectrum by division).  A seeded sample of 24 spectra plus
     the first and the last is compared with the oracle element by element, paths and argmax
     included."""
     B, N, H = 1024, 1 << 17, 32

@@ -101,8 +101,8 @@ def test_tail_batch_dtypes_and_shapes(hs, oracle_lib, dtype):
 
 
 def test_tail_per_spectrum_norm(hs, oracle_lib):
-    """Per-spectrum normalisation rows reach both tail kernels (the generic one and the one-order
-    one), several one-order tiles per spectrum, uneven lengths."""
+    """Per-spectrum normalisation rows reach both kinds of tail tile (generic and one-order),
+    several one-order tiles per spectrum, uneven lengths (spectrum found by binary search)."""
     xs = [synth.spectrum(n, 500 + n % 17, [synth.Pulsar(41.3, 0.06)]) for n in (5000, 40000, 20011, 9000)]
     plan, _, _ = tail_case(hs, oracle_lib, xs, 16, hs.SIMPLE | hs.GREEDY, per_spec_norm=True)
     plan.close()
