@@ -722,8 +722,6 @@ hs_status enqueue_fwd(hs_plan p, const void *spectra, const float *w, const hs_f
         a.tail_tiles_per_spec = static_cast<uint32_t>(p->tail_tile_start.back() / p->d.num_spectra);
         a.tail1_tiles_per_spec = static_cast<uint32_t>(p->tail1_tile_start.back() / p->d.num_spectra);
         a.inv_tiles_per_spec = a.tiles_per_spec ? 1.0f / static_cast<float>(a.tiles_per_spec) : 0.f;
-        a.inv_tail_tiles_per_spec = a.tail_tiles_per_spec ? 1.0f / static_cast<float>(a.tail_tiles_per_spec) : 0.f;
-        a.inv_tail1_tiles_per_spec = a.tail1_tiles_per_spec ? 1.0f / static_cast<float>(a.tail1_tiles_per_spec) : 0.f;
     }
     a.H = p->d.H;
     a.mitigation = (p->d.flags & HS_FLAG_NO_MITIGATION) ? 0 : 1;

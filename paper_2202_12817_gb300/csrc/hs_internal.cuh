@@ -51,9 +51,7 @@ struct Fwd1DArgs {
                                    // all, fewer than 2^22 tiles in all)
     uint32_t tail_tiles_per_spec;  // > 0: likewise for the truncated-tail tiles
     uint32_t tail1_tiles_per_spec; // > 0: likewise for the one-order tail tiles
-    float inv_tiles_per_spec;      // fl(1 / tiles_per_spec), fl(1 / tail_tiles_per_spec), ...
-    float inv_tail_tiles_per_spec;
-    float inv_tail1_tiles_per_spec;
+    float inv_tiles_per_spec;      // fl(1 / tiles_per_spec)
     int32_t H;
     int32_t mitigation;
     int32_t per_spectrum_norm;
