@@ -23,7 +23,7 @@ static_assert(kTailTile == kTailThreads * kTailChains, "host tail tiling and ker
 // Generic tile `tile` (of the tail_tile_start numbering) of spectrum s: kTailThreads x
 // kTailChains consecutive fundamentals N_f <= n < n1, both forms in one thread.  Most of them
 // have a few orders only, so a thread's time is a short chain of dependent loads: each thread
-// runs kTailChains fundamentals (n, n + T, ...) interleaved order by order to keep that many
+// runs kTailChains fundamentals (n, n + 32, ...) interleaved order by order to keep that many
 // chains in flight.  The tiles of spectrum s bring spectrum s - kTailAhead into L2, one share
 // each.
 template <typename T, int FORMS, bool WHITEN>
@@ -41,7 +41,10 @@ __device__ __forceinline__ void tail_orders(const Fwd1DArgs &a, const int s, con
     // order 1 only (tail_one_order)
     const int64_t n_all = __ldg(a.fund_off + s + 1) - fbase, n1 = (len - 1) / 2 + 1;
     const int64_t nf = n_all < n1 ? n_all : n1;
-    const int64_t nbase = __ldg(a.nf_main + s) + (tile - t0) * (static_cast<int64_t>(blockDim.x) * CH) + threadIdx.x;
+    // warp w runs the 32 CH fundamentals [32 CH w, 32 CH (w + 1)) of the tile, chain c of lane l at 32 c + l, so a
+    // thread's chains have nearly the same order counts
+    const int64_t nbase = __ldg(a.nf_main + s) + (tile - t0) * (static_cast<int64_t>(blockDim.x) * CH) +
+                          (threadIdx.x >> 5) * (32 * CH) + (threadIdx.x & 31);
     const T *x = static_cast<const T *>(a.x) + __ldg(a.in_off + s);
     const float *wv = a.w;
     RunMax ms[CH], mg[CH];
@@ -51,7 +54,7 @@ __device__ __forceinline__ void tail_orders(const Fwd1DArgs &a, const int s, con
     int Hmax = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-        const int64_t n = nbase + static_cast<int64_t>(c) * blockDim.x;
+        const int64_t n = nbase + static_cast<int64_t>(c) * 32;
         ms[c] = RunMax{0.f, 1};
         mg[c] = RunMax{0.f, 1};
         bits[c] = 0;
@@ -131,7 +134,7 @@ __device__ __forceinline__ void tail_orders(const Fwd1DArgs &a, const int s, con
     unsigned long long ks = 0ull, kg = 0ull;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
-        const int64_t n = nbase + static_cast<int64_t>(c) * blockDim.x;
+        const int64_t n = nbase + static_cast<int64_t>(c) * 32;
         if (n >= nf) continue;
         const int64_t o = fbase + n;
         if (kS) {
