@@ -83,3 +83,18 @@ def test_tail_tiling(lengths, H):
     for N, c in zip(lengths, seen):
         nf_main = (N - 1) // H
         assert np.all(c[:nf_main] == 0) and np.all(c[nf_main:N - 1] == 1) and c[N - 1] == 0
+
+
+def test_generic_tile_chain_mapping():
+    """Within a generic tile, warp w runs fundamentals [128 w, 128 w + 128) and lane l's chain c is
+    32 c + l of them: the 256 threads x 4 chains cover the 1024 fundamentals of the tile once, and a
+    thread's chains lie within 96 fundamentals of each other."""
+    threads, chains = 256, 4
+    assert threads * chains == GENERIC_TILE
+    seen = np.zeros(GENERIC_TILE, np.int32)
+    for t in range(threads):
+        ns = [(t >> 5) * (32 * chains) + c * 32 + (t & 31) for c in range(chains)]
+        assert max(ns) - min(ns) == 32 * (chains - 1)
+        for n in ns:
+            seen[n] += 1
+    assert np.all(seen == 1)
